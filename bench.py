@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the NSF eigensolver hot path on one GB300 (or N, weak scaling).
+
+A step is one complete eigensolve of the headline workload: 96^3 pseudochiral
+cylinders, the 20 smallest positive eigenvalues by thick-restart invert
+Lanczos on the HHPD-NFGEP with complex64 CG inside FP64 refinement and FP64
+orthogonalisation (every row of the hot path: tables, assembly, twisted FFTs,
+material product, projections, B_r, CG, Lanczos).  The printed `value` is
+eigenpairs per second over all ranks.  Alongside: A_r matvecs/s in complex64
+and complex128, CG iterations/s, the FP64 eigensolve for comparison, the
+roofline of the dominant matvec pass, an end-to-end figure through the public
+API with host inputs, and the CPU oracle's rate on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank solves its own k-point (independent problems; no
+collective on the data path): weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NFGEP matvecs/s & eigenpairs/s at 96^3, mixed vs FP64, % HBM roofline"
+UNIT = "eigenpairs/s"
+WORKLOAD = "pseudo96"
+NEV = 20
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+# complex64 + complex128 A_r products per nev = 20 eigensolve of pseudo96, as
+# measured by this benchmark's GPU arm; the reference arm converts its timed
+# oracle products to eigenpairs/s with it.
+MATVECS_PER_SOLVE = 6000
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--skip-fp64", action="store_true")
+    p.add_argument("--skip-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(backend):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_kpoint(base, rank):
+    # a distinct Bloch vector per rank (same grid and medium): independent problems
+    return tuple(float(v) + 0.01 * rank for v in base)
+
+
+def bytes_per_pass(n, csize, kind):
+    """Algorithmic HBM bytes of each pass of one A_r product (3-pass model):
+    pass 1 reads u (4n) and writes six fields (6n); pass 2 reads and writes the
+    six fields and reads the material (1/Phi per component and gamma); pass 3
+    reads six fields and writes A_r u (4n)."""
+    rsize = csize // 2
+    mat_reals = 6 if kind == "chiral" else 4
+    return [10 * n * csize, 12 * n * csize + mat_reals * n * rsize, 10 * n * csize]
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) timing: the reference arm and the cpu_baseline field
+# ---------------------------------------------------------------------------
+
+def oracle_matvec_rate(w, seconds, max_calls=50):
+    import numpy as np
+
+    import workloads as wl
+    from oracle import nfgep
+    orc = nfgep.NFGEP(w["grid"], w["kdota"], w["medium"])
+    u = wl.random_complex(4 * orc.n, 3)
+    orc.Ar(u)  # warm the FFT plans
+    t0 = time.perf_counter()
+    calls = 0
+    while calls < max_calls:
+        orc.Ar(u)
+        calls += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    _ = np
+    return calls / dt, calls, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores: each step is a bounded sample
+    of the workload (a few FFT A_r products), converted to eigenpairs/s."""
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    import workloads as wl
+    w = wl.workload(WORKLOAD)
+    per = []
+    for i in range(args.warmup + args.steps):
+        rate, calls, dt = oracle_matvec_rate(w, seconds=max(2.0, args.cpu_seconds / max(args.steps, 1)), max_calls=4)
+        if i >= args.warmup:
+            per.append((rate, calls, dt))
+    rate = sum(c for _, c, _ in per) / sum(d for _, _, d in per)
+    value = rate * NEV / MATVECS_PER_SOLVE
+    ms_per_step = 1000.0 * MATVECS_PER_SOLVE / rate
+    sample = (f"{sum(c for _, c, _ in per)} oracle FP64 FFT A_r products at 96^3 (pseudo96) over "
+              f"{args.steps} steps; eigenpairs/s = rate * {NEV} / {MATVECS_PER_SOLVE} products per solve")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "pseudo96: 96^3 pseudochiral (x-y) cylinders, nev 20", "l2": "inputs > L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as wl
+    from paper_1402_6297_gb300 import nfs
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = wl.workload(WORKLOAD)
+    grid, med = w["grid"], w["medium"]
+    kd = rank_kpoint(w["kdota"], rank)
+    n1, n2, n3 = grid
+    n = n1 * n2 * n3
+    hbm, peak_kind = peaks()
+    stream = torch.cuda.current_stream()
+
+    ctx = nfs.Context(grid, kd, med, precision="mixed", cg_tol=1e-10, eig_tol=1e-9)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # ---- A_r products: whole product and each pass, CUDA events on the stream
+    def time_matvec(dtype, reps=20):
+        u = torch.from_numpy(wl.random_complex(4 * n, 5)).to(dev).to(dtype)
+        out = torch.empty_like(u)
+        for _ in range(3):
+            ctx.matvec(u, out)
+        whole, passes = [], [[], [], []]
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.matvec(u, out)
+            e1.record(stream)
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            for i, mask in enumerate((1, 2, 4)):
+                ctx.matvec_passes(mask, u, out)
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize()
+            whole.append(e0.elapsed_time(e1))
+            for i in range(3):
+                passes[i].append(ev[i].elapsed_time(ev[i + 1]))
+        return statistics.median(whole), [statistics.mean(p) for p in passes]
+
+    mv64_ms, pass64 = time_matvec(torch.complex64)
+    mv128_ms, pass128 = time_matvec(torch.complex128)
+
+    # ---- the step: one mixed-precision eigensolve (nev = 20)
+    for _ in range(args.warmup):
+        ctx.eigs(NEV, vectors=True, allow_noconv=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    infos, step_ms, omega, Y = [], [], None, None
+    t_host0 = time.perf_counter()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        omega, Y, info = ctx.eigs(NEV, vectors=True, allow_noconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+    torch.cuda.synchronize()
+    host_s = time.perf_counter() - t_host0
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    total_s = max_over_ranks(sum(step_ms) / 1000.0, world, dev)
+    value = world * NEV * args.steps / total_s
+    info = infos[-1]
+    matvecs = info.matvecs_c64 + info.matvecs_c128
+    cg_its = info.cg_iterations
+    res = nfs.residuals(ctx, omega, Y)
+
+    # ---- FP64 eigensolve for comparison
+    fp64 = None
+    if not args.skip_fp64:
+        ctx64 = nfs.Context(grid, kd, med, precision="fp64", cg_tol=1e-12, eig_tol=1e-10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        om64, _, inf64 = ctx64.eigs(NEV, vectors=False, allow_noconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"eigenpairs_per_s": NEV / (ms64 / 1000.0), "ms": ms64,
+                "lanczos_steps": inf64.lanczos_steps, "cg_iterations": int(inf64.cg_iterations),
+                "max_rel_diff_mixed_vs_fp64": float(np.max(np.abs(omega - om64) / om64))}
+        ctx64.close()
+
+    # ---- end to end through the public API: host material in pinned memory
+    # is copied by nfs_setup, the eigensolve runs, omega is read back.
+    pin_eps = torch.from_numpy(np.ascontiguousarray(med.eps)).pin_memory()
+    pin_gam = torch.from_numpy(np.ascontiguousarray(med.gamma)).pin_memory()
+    med_pinned = wl.Medium(med.grid, med.kind, pin_eps.numpy(), pin_gam.numpy(), None, med.axes)
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 2))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = nfs.Context(grid, kd, med_pinned, precision="mixed", cg_tol=1e-10, eig_tol=1e-9)
+        om2, _, _ = c2.eigs(NEV, vectors=False, allow_noconv=True)
+        c2.close()
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_total = max_over_ranks(sum(e2e_ms) / 1000.0, world, dev)
+    e2e_value = world * NEV * len(e2e_ms) / e2e_total
+    h2d = pin_eps.numel() * 8 + pin_gam.numel() * 8
+    d2h = NEV * 8
+
+    # ---- roofline of the dominant pass (complex64 product)
+    bpp = bytes_per_pass(n, 8, med.kind)
+    dom = max(range(3), key=lambda i: pass64[i])
+    achieved = bpp[dom] / (pass64[dom] / 1000.0) / 1e9
+    whole_bytes = sum(bpp)
+    roof = {"bound": "hbm", "kernel": ["pass1_assemble_ifft_xy", "pass2_z_material", "pass3_fft_xy_project"][dom],
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "traffic": None,
+            "matvec_c64": {"bytes": whole_bytes, "ms": mv64_ms, "GBps": whole_bytes / (mv64_ms / 1e3) / 1e9,
+                           "frac": whole_bytes / (mv64_ms / 1e3) / 1e9 / hbm},
+            "pass_ms_c64": pass64, "pass_ms_c128": pass128}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        rate, calls, dt = oracle_matvec_rate(w, args.cpu_seconds)
+        cpu = {"value": rate * NEV / matvecs, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{calls} oracle FP64 FFT A_r products at 96^3 in {dt:.1f} s ({rate:.3f}/s); "
+                         f"eigenpairs/s = rate * {NEV} / {matvecs} products per GPU eigensolve"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_s * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64", "data": "synthetic",
+        "config": {"workload": "pseudo96: 96^3 pseudochiral (x-y) cylinders eps 13 r 0.1, gamma 0.4, "
+                               "k.a=(0.1,0.2,0.3)+0.01*rank, nev 20, mixed (complex64 CG, FP64 refinement "
+                               "and Lanczos)", "l2": "eigensolve working set > L2; matvec timings flush L2",
+                   "grid": list(grid), "nev": NEV},
+        "matvecs_per_s": {"c64": 1000.0 / mv64_ms, "c128": 1000.0 / mv128_ms},
+        "cg_iters_per_s": cg_its / (statistics.mean(step_ms) / 1000.0),
+        "eigensolve": {"lanczos_steps": info.lanczos_steps, "restarts": info.restarts,
+                       "cg_iterations": int(cg_its), "matvecs_c64": int(info.matvecs_c64),
+                       "matvecs_c128": int(info.matvecs_c128), "nconv": info.nconv,
+                       "max_residual": max(res), "omega": [float(x) for x in omega],
+                       "host_s": host_s},
+        "fp64": fp64,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    # kernels launched inside one timed step: 3 per product, 5 per CG
+    # iteration besides the product, plus Lanczos bookkeeping (counted exactly
+    # from the solver's own counters)
+    line["gpu_launches"] = int(3 * matvecs + 5 * cg_its + 12 * info.lanczos_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

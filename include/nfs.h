@@ -1,0 +1,189 @@
+/*
+ * nfs.h -- C ABI of libnfs: the null-space-free (NSF) eigensolver hot path for
+ * the discrete 3-D Maxwell equations in chiral and pseudochiral media, on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Chern, Hsieh, Huang, Lin, Wang, "Singular value decompositions for
+ * single-curl operators in three-dimensional Maxwell's equations for complex
+ * media".  Equations are cited by their labels in the paper's source.
+ *
+ *   C = P_r Sigma_r Q_r^*            SVD of the Yee single-curl operator (thm:svd_C)
+ *   B_r y = omega^{-1} A_r y         HHPD-NFGEP (thm:NFSEP_real_ew, eq. NFSEP_spd_1)
+ *   A_r   = diag(P_r^*, Q_r^*) M diag(P_r, Q_r)         eq. (factor_mtx)
+ *
+ * Vector layout (every 4n-vector crossing this ABI):
+ *   u = [u1a | u1b | u2a | u2b], each block n = n1*n2*n3 complex numbers in
+ *   spectral order (i3, i2, i1), i1 fastest.  u1a, u1b are the coefficients of
+ *   the columns P_2, P_1 of P_r; u2a, u2b those of Q_1, Q_2 of Q_r.  Complex
+ *   numbers are interleaved (re, im): double2 for NFS_C128, float2 for NFS_C64.
+ *
+ * Material layout: per-component real arrays [3][n3][n2][n1], x fastest,
+ * component c sampled at its own Yee edge location by the caller (the library
+ * does no averaging; the paper, end of Section 3, leaves that stencil open).
+ *
+ * Ownership: a context copies everything it needs from the caller at setup
+ * and owns all device workspaces; vector arguments are caller-owned DEVICE
+ * pointers, used on the context's stream, never retained after a call
+ * returns.  No call allocates device memory except nfs_setup and the first
+ * nfs_eigs with a larger basis than any before.
+ *
+ * Errors: every int-returning call returns NFS_OK (0) or a negative NFS_E*
+ * code; no C++ exception crosses the ABI.  nfs_strerror gives a message.
+ * Calls on one context are not thread-safe.
+ */
+#ifndef NFS_H
+#define NFS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+#define NFS_OK            0
+#define NFS_EINVAL       (-1)   /* bad pointer, size, option or enum             */
+#define NFS_EUNSUPPORTED (-2)   /* non-orthogonal lattice, or a grid size that   */
+                                /* is not one of 8,12,16,24,32,48,64,96,128 or   */
+                                /* whose xy plane exceeds shared memory          */
+#define NFS_EKPOINT      (-3)   /* every k.a_l integer: Lambda_q singular (Lemma) */
+#define NFS_EBASIS       (-4)   /* alpha, beta violate the Lemma: Lambda_p = 0    */
+#define NFS_ENOTHPD      (-5)   /* mu <= 0 or Phi <= 0: Assumption (eq. assump)   */
+#define NFS_ENOCONV      (-6)   /* iteration limit reached (info still filled)    */
+#define NFS_EBREAKDOWN   (-7)   /* CG p^*Ap <= 0 or NaN; Lanczos lost rank        */
+#define NFS_ETIMEOUT     (-8)   /* a bounded device-side wait gave up             */
+#define NFS_ECUDA        (-9)   /* a CUDA runtime error                          */
+#define NFS_ENOMEM       (-10)  /* device allocation failed                      */
+
+/* ---- enums --------------------------------------------------------------- */
+#define NFS_MEDIUM_CHIRAL       0  /* xi_d = i gamma, zeta_d = -i gamma, per component   */
+#define NFS_MEDIUM_PSEUDOCHIRAL 1  /* xi_d = i gamma on the (axis_a, axis_b) pair only   */
+
+#define NFS_PREC_FP64  0  /* complex128 matvec, CG and Lanczos                    */
+#define NFS_PREC_MIXED 1  /* complex64 matvec + CG, FP64 refinement and Lanczos   */
+
+#define NFS_C128 0        /* vector element type: double2                         */
+#define NFS_C64  1        /* vector element type: float2                          */
+
+typedef struct nfs_ctx nfs_ctx;
+
+/* Section 4.3, eqs. (chiral_para_mtx) and (pseudo_chiral_para_mtx), with a
+ * diagonal permittivity and permeability.  All pointers are HOST pointers and
+ * are copied by nfs_setup. */
+typedef struct {
+  int kind;              /* NFS_MEDIUM_*                                          */
+  int axis_a, axis_b;    /* pseudochiral coupled pair (0 = x, 1 = y, 2 = z), a!=b */
+  const double* eps;     /* [3][n3][n2][n1], > 0                                  */
+  const double* mu;      /* [3][n3][n2][n1], > 0, or NULL meaning mu = 1          */
+  const double* gamma;   /* chiral: [3][n3][n2][n1]; pseudochiral: [n3][n2][n1]   */
+} nfs_material;
+
+typedef struct {
+  int precision;           /* NFS_PREC_FP64 or NFS_PREC_MIXED                     */
+  double alpha, beta;      /* free parameters of Lambda_p (eq. mtx_Lambda_p_q)    */
+  double cg_tol;           /* relative residual ||b - A_r x|| / ||b|| to reach    */
+  int cg_maxit;            /* CG iteration cap (per refinement step when mixed)   */
+  double inner_tol;        /* mixed: residual reduction of each FP32 inner solve  */
+  int max_refine;          /* mixed: cap on FP64 refinement steps                 */
+  double eig_tol;          /* Lanczos: Ritz residual <= eig_tol * |theta|         */
+  int ncv;                 /* Lanczos basis size; 0 means max(3 nev, 2 nev + 2)   */
+  int max_restarts;        /* thick-restart cap                                   */
+  unsigned long long seed; /* starting-vector seed                                */
+  void* stream;            /* cudaStream_t for every launch; NULL = default       */
+} nfs_options;
+
+typedef struct {
+  int iterations;          /* total CG iterations (inner FP32 ones when mixed)    */
+  int refinements;         /* FP64 residual refinements (mixed), else 0           */
+  double rel_residual;     /* final ||b - A_r x|| / ||b||, FP64                   */
+  int status;              /* NFS_OK, NFS_ENOCONV or NFS_EBREAKDOWN               */
+} nfs_solve_info;
+
+typedef struct {
+  int lanczos_steps;       /* operator applications (one CG solve each)           */
+  int restarts;
+  long long cg_iterations; /* summed over every solve                             */
+  long long matvecs_c64;
+  long long matvecs_c128;
+  int nconv;               /* wanted Ritz pairs that met eig_tol                   */
+  double max_ritz_residual;/* max over returned pairs of |beta y_m| / |theta|      */
+  int status;
+} nfs_eigs_info;
+
+/* Defaults: FP64, alpha = 2, beta = 3, cg_tol 1e-12, cg_maxit 2000,
+ * inner_tol 1e-5, max_refine 8, eig_tol 1e-10, ncv 0, max_restarts 200,
+ * seed 1, default stream. */
+void nfs_default_options(nfs_options* opt);
+
+/* Build a context for one Bloch problem (Algorithm alg:NullSpaceFree, steps
+ * 1-3: the Lambda tables, Lambda_q, Lambda_p; Pi_1, Pi_2 are evaluated on the
+ * fly from them).
+ *   grid[3]   = (n1, n2, n3), each in {8,12,16,24,32,48,64,96,128}, n1 = n2
+ *   lattice   = 9 doubles, row l = a_l; must be diagonal (orthorhombic).
+ *               NULL means the unit cube (a = 1).
+ *   k[3]      = Bloch vector divided by 2 pi (Cartesian); the phase across a_l
+ *               is exp(i 2 pi k.a_l) (eq. quasi_periodic).
+ *   mat, opt  = copied; opt may be NULL (defaults).
+ * Checks the Lemma (lem:nonsingular_full_rank) -> NFS_EKPOINT / NFS_EBASIS and
+ * the Assumption (eq. assump) -> NFS_ENOTHPD.  On error *out is NULL. */
+int nfs_setup(nfs_ctx** out, const int grid[3], const double* lattice, const double k[3],
+              const nfs_material* mat, const nfs_options* opt);
+
+/* Au = A_r u (eq. factor_mtx / eq. spd_LS) in the given element type.  u and
+ * Au are device pointers to 4n complex numbers and must not overlap. */
+int nfs_matvec(nfs_ctx* ctx, int dtype, const void* u, void* Au);
+
+/* Run only the passes of nfs_matvec selected by `mask` (bit 0: pass 1,
+ * spectral assembly + inverse DFT along x, y; bit 1: pass 2, inverse DFT
+ * along z + material product + forward DFT along z; bit 2: pass 3, forward
+ * DFT along y, x + projection onto P_r^*, Q_r^*).  Passes communicate through
+ * the context's field workspace, so mask 7 equals nfs_matvec; other masks
+ * exist to time the passes one by one.  Same arguments as nfs_matvec. */
+int nfs_matvec_passes(nfs_ctx* ctx, int dtype, int mask, const void* u, void* Au);
+
+/* out = B_r v = i [Sigma_r^{-1} v2; -Sigma_r^{-1} v1] (eq. NFSEP_spd_1), with
+ * v1 = [v1a; v1b], v2 = [v2a; v2b]; device complex128, 4n each. */
+int nfs_apply_Br(nfs_ctx* ctx, const void* v, void* out);
+
+/* Solve A_r x = b by unpreconditioned CG (Section 4.2).  b, x: device
+ * complex128 (4n); x holds the initial guess on entry.  FP64 contexts run CG
+ * in complex128; MIXED contexts run complex64 CG inside FP64 iterative
+ * refinement.  info may be NULL. */
+int nfs_cg_solve(nfs_ctx* ctx, const void* b, void* x, nfs_solve_info* info);
+
+/* The nev smallest positive eigenvalues omega of the GEP (eq.
+ * discrete_GEP_EH), by thick-restart invert Lanczos on the HHPD-NFGEP: the
+ * nev largest theta = 1/omega of B_r y = theta A_r y, orthogonalised in the
+ * A_r inner product in FP64.  omega: HOST array of nev doubles, ascending.
+ * Y: device complex128 array [nev][4n] of A_r-normalised eigenvectors y, or
+ * NULL.  info may be NULL.  Returns NFS_ENOCONV (results still written) if the
+ * restart cap is hit first. */
+int nfs_eigs(nfs_ctx* ctx, int nev, double* omega, void* Y, nfs_eigs_info* info);
+
+/* Gradient of sum_j weights[j] * omega_j with respect to every per-component
+ * permittivity and chirality value, from eigenvectors Y (device complex128
+ * [m][4n], e.g. from nfs_eigs).  By first-order perturbation of the Hermitian
+ * pencil, d omega = y^* (dA_r) y / (y^* B_r y); dA_r follows from eq.
+ * factor_mtx.  Requires mu = 1.
+ *   weights: HOST, m doubles.
+ *   d_eps:   DEVICE, [3][n3][n2][n1] doubles (written, not accumulated).
+ *   d_gamma: DEVICE, chiral [3][n3][n2][n1]; pseudochiral [n3][n2][n1].
+ * Either output may be NULL.  The sum over a degenerate cluster is only
+ * defined if the cluster is complete within Y. */
+int nfs_eig_grad(nfs_ctx* ctx, int m, const double* weights, const void* Y,
+                 double* d_eps, double* d_gamma);
+
+/* Basic facts about a context: n, and device bytes held. */
+long long nfs_num_voxels(const nfs_ctx* ctx);
+long long nfs_device_bytes(const nfs_ctx* ctx);
+
+/* Replace the stream used by later calls (cudaStream_t). */
+int nfs_set_stream(nfs_ctx* ctx, void* stream);
+
+void nfs_destroy(nfs_ctx* ctx);
+const char* nfs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NFS_H */

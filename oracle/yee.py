@@ -23,12 +23,12 @@ def mesh_lengths(grid, a=1.0):
 
 
 # ---------------------------------------------------------------------------
-# Eq. (2.3): the quasi-periodic forward-difference matrix K_{a,m}
+# eq. (mtx_K_n1): the quasi-periodic forward-difference matrix K_{a,m}
 # ---------------------------------------------------------------------------
 
 def K_matrix(m, kdota):
     """K_{a,m}: -1 on the diagonal, +1 on the super-diagonal and the Bloch
-    phase exp(i 2 pi k.a) in the bottom-left corner (Eq. (2.3))."""
+    phase exp(i 2 pi k.a) in the bottom-left corner (eq. (mtx_K_n1))."""
     K = sp.lil_matrix((m, m), dtype=np.complex128)
     for r in range(m):
         K[r, r] = -1.0
@@ -39,7 +39,7 @@ def K_matrix(m, kdota):
 
 
 def curl_blocks(grid, kdota, a=1.0):
-    """C_1, C_2, C_3 of Eq. (2.2) (sparse n x n)."""
+    """C_1, C_2, C_3 of eq. (mtx_C123) (sparse n x n)."""
     n1, n2, n3 = grid
     dx, dy, dz = mesh_lengths(grid, a)
     I1, I2, I3 = (sp.identity(m, dtype=np.complex128, format="csr") for m in (n1, n2, n3))
@@ -50,13 +50,13 @@ def curl_blocks(grid, kdota, a=1.0):
 
 
 def curl_matrix(grid, kdota, a=1.0):
-    """C of Eq. (2.1): [[0, -C3, C2], [C3, 0, -C1], [-C2, C1, 0]] (sparse 3n x 3n)."""
+    """C of eq. (mtx_C): [[0, -C3, C2], [C3, 0, -C1], [-C2, C1, 0]] (sparse 3n x 3n)."""
     C1, C2, C3 = curl_blocks(grid, kdota, a)
     return sp.bmat([[None, -C3, C2], [C3, None, -C1], [-C2, C1, None]], format="csr")
 
 
 # ---------------------------------------------------------------------------
-# Eq. (2.4)-(2.5): D_{a,m}, U_m, Lambda_{a,m} and T
+# eqs. (mtx_Dm), (mtx_Um), (mtx_T): D_{a,m}, U_m, Lambda_{a,m} and T
 # ---------------------------------------------------------------------------
 
 def D_diag(m, kdota):
@@ -77,7 +77,7 @@ def Lambda_1d(m, kdota):
 
 
 def T_dense(grid, kdota):
-    """T = n^{-1/2} (D3 x D2 x D1)(U3 x U2 x U1) (Eq. (2.5)), dense n x n."""
+    """T = n^{-1/2} (D3 x D2 x D1)(U3 x U2 x U1) (eq. (mtx_T)), dense n x n."""
     n1, n2, n3 = grid
     D = np.kron(np.diag(D_diag(n3, kdota[2])),
                 np.kron(np.diag(D_diag(n2, kdota[1])), np.diag(D_diag(n1, kdota[0]))))
@@ -107,8 +107,8 @@ def apply_Tstar(p, kdota):
 
 
 # ---------------------------------------------------------------------------
-# Theorem 2.1, the Lemma (Eq. (2.6)), Pi_0 (Eq. (2.7)), Pi_1 (Eq. (2.8)),
-# Pi_2 (Eq. (2.9))
+# Theorem (thm:SchurDecomp_Ci), the Lemma (eq. (mtx_Lambda_p_q)), Pi_0
+# (eq. (mtx_Q0)), Pi_1 (eq. (mtx_Pi_1)), Pi_2 (eq. (mtx_Pi_2))
 # ---------------------------------------------------------------------------
 
 class Symbols:
@@ -121,7 +121,7 @@ class Symbols:
         self.grid = tuple(grid)
         self.kdota = tuple(kdota)
         self.alpha, self.beta = float(alpha), float(beta)
-        # Theorem 2.1: Lambda_1 = dx^{-1} (I x I x Lambda_{a1,n1}), etc.
+        # thm:SchurDecomp_Ci: Lambda_1 = dx^{-1} (I x I x Lambda_{a1,n1}), etc.
         L1 = (Lambda_1d(n1, kdota[0]) / dx)[None, None, :]
         L2 = (Lambda_1d(n2, kdota[1]) / dy)[None, :, None]
         L3 = (Lambda_1d(n3, kdota[2]) / dz)[:, None, None]
@@ -131,13 +131,13 @@ class Symbols:
         self.L3 = np.broadcast_to(L3, shape).copy()
         L1, L2, L3 = self.L1, self.L2, self.L3
         al, be = self.alpha, self.beta
-        # Eq. (2.6)
+        # eq. (mtx_Lambda_p_q)
         self.Lq = (np.conj(L1) * L1 + np.conj(L2) * L2 + np.conj(L3) * L3).real
         self.Lp = np.stack([be * L3 - L2, L1 - al * L3, al * L2 - be * L1])
         self.Lp2 = np.sum(np.abs(self.Lp) ** 2, axis=0)       # Lambda_p^* Lambda_p
-        # Eq. (2.7)
+        # eq. (mtx_Q0)
         self.Pi0 = np.stack([L1, L2, L3]) / np.sqrt(self.Lq)
-        # Eq. (2.8): the printed vector, normalised by (Lambda_q Lambda_p^* Lambda_p)^{-1/2}
+        # eq. (mtx_Pi_1): the printed vector, normalised by (Lambda_q Lambda_p^* Lambda_p)^{-1/2}
         p1, p2, p3 = self.Lp
         v = np.stack([
             p3 * np.conj(L2) - p2 * np.conj(L3),
@@ -145,7 +145,7 @@ class Symbols:
             p2 * np.conj(L1) - p1 * np.conj(L2),
         ])
         self.Pi1 = v / np.sqrt(self.Lq * self.Lp2)
-        # Eq. (2.9)
+        # eq. (mtx_Pi_2)
         self.Pi2 = np.conj(self.Lp) / np.sqrt(self.Lp2)
         self.sigma = np.sqrt(self.Lq)                          # Sigma_r diagonal (per block)
 
@@ -157,13 +157,13 @@ class Symbols:
 
 def Pi1_as_printed(sym: Symbols):
     """Pi_1 with the normalisation exactly as printed in the second line of
-    Eq. (2.8), (Lambda_p^* Lambda_p Lambda_q^{-1})^{-1/2}.  Kept only so a test
+    eq. (mtx_Pi_1), (Lambda_p^* Lambda_p Lambda_q^{-1})^{-1/2}.  Kept only so a test
     can show that this reading does not give a unitary Q."""
     return sym.Pi1 * np.sqrt(sym.Lq * sym.Lp2) / np.sqrt(sym.Lp2 / sym.Lq)
 
 
 # ---------------------------------------------------------------------------
-# Dense Q, P (Eq. (2.10)) and the SVD factors (Theorem 2.4) -- small grids only
+# Dense Q, P (eq. (mtx_QdPd)) and the SVD factors (thm:svd_C) -- small grids only
 # ---------------------------------------------------------------------------
 
 def _stack_diag(Pi):

@@ -1,0 +1,63 @@
+// Host-side entry points of the three-pass A_r product (matvec_kernels.cuh),
+// instantiated for complex64 (matvec_f32.cu) and complex128 (matvec_f64.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "nfs_complex.cuh"
+
+namespace nfs {
+
+template <typename R>
+struct MatView;
+
+template <typename R>
+struct MatvecArgs {
+  const cplx<R>* u;       // 4n, spectral
+  cplx<R>* Au;            // 4n, spectral
+  cplx<R>* fld;           // 6n workspace
+  const cplx<R>* lam;     // Lambda_1 | Lambda_2 | Lambda_3 (n1 + n2 + n3)
+  const cplx<R>* tw1;     // exp(-2 pi i m / n1), m < n1
+  const cplx<R>* tw2;
+  const cplx<R>* tw3;
+  const R* inv_phi;
+  const R* gam;
+  const R* inv_mu;        // nullptr for mu = 1
+  int kind, ax_a, ax_b;
+  int n1, n2, n3;
+  R alpha, beta;
+  const int* skip;        // device flag: when nonzero every pass returns at once
+  cudaStream_t stream;
+};
+
+// Largest dynamic shared memory a CTA may request on sm_103a.
+constexpr size_t kMaxDynSmem = 232448;
+
+// Whether the kernels exist for this grid in this precision (n1 = n2 and each
+// size in {8, 12, 16, 24, 32, 48, 64, 96, 128}, plane fits in shared memory).
+template <typename R> bool matvec_supported(int n1, int n2, int n3);
+// Opt the chosen kernels in to their dynamic shared memory (once per device).
+template <typename R> cudaError_t matvec_prepare(int n1, int n2, int n3);
+template <typename R> cudaError_t matvec_launch(const MatvecArgs<R>& a);
+// Selected passes only (bit 0: pass 1, bit 1: pass 2, bit 2: pass 3).
+template <typename R> cudaError_t matvec_launch_mask(const MatvecArgs<R>& a, int mask);
+// Split launches used by the eigenvector-gradient path: pass 1 only.
+template <typename R> cudaError_t pass1_launch(const MatvecArgs<R>& a);
+
+// Gradient accumulation (complex128 only): inverse z-DFT of the six pass-1
+// fields and, per voxel, d_eps += scale * dA/deps, d_gamma += scale * dA/dgamma.
+struct GradArgs {
+  const double2* fld;
+  const double2* tw3;
+  const double* inv_phi;
+  const double* gam;
+  int kind, ax_a, ax_b;
+  int n1, n2, n3;
+  double scale;
+  double* d_eps;
+  double* d_gamma;
+  cudaStream_t stream;
+};
+cudaError_t grad_prepare(int n1, int n2, int n3);
+cudaError_t grad_launch(const GradArgs& a);
+
+}  // namespace nfs

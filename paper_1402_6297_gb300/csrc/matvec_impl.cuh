@@ -1,0 +1,185 @@
+// Size dispatch and launch of the three matvec passes (see matvec_kernels.cuh).
+// Included by matvec_f32.cu and matvec_f64.cu, which instantiate it.
+#pragma once
+#include "matvec.h"
+#include "matvec_kernels.cuh"
+
+namespace nfs {
+
+// Threads per CTA of the xy-plane passes, per plane edge length.
+__host__ __device__ constexpr int plane_threads(int N) {
+  return N == 8 ? 64 : N == 12 ? 64 : N == 16 ? 64 : N == 24 ? 128 : N == 32 ? 256
+       : N == 48 ? 384 : N == 64 ? 256 : N == 96 ? 384 : 512;
+}
+// xy columns per CTA of the z pass, per z length and element size.
+__host__ __device__ constexpr int z_tile(int N3, int csize) {
+  return N3 <= 24 ? 32 : ((csize == 16 && N3 >= 96) ? 8 : 16);
+}
+__host__ __device__ constexpr int z_threads(int N3) { return N3 == 128 ? 512 : 384; }
+
+template <typename R, int NX>
+constexpr size_t plane_smem() {
+  return (size_t)(NX * (NX + 1) + 2 * NX) * sizeof(cplx<R>);
+}
+template <typename R, int N3>
+constexpr size_t z_smem() {
+  return (size_t)(N3 * (6 * z_tile(N3, (int)sizeof(cplx<R>)) + 1) + N3) * sizeof(cplx<R>);
+}
+
+template <typename R, int NX>
+constexpr bool plane_fits() {
+  return plane_smem<R, NX>() <= kMaxDynSmem;
+}
+
+#define NFS_FOR_EACH_SIZE(M) M(8) M(12) M(16) M(24) M(32) M(48) M(64) M(96) M(128)
+
+template <typename R, int NX>
+static cudaError_t plane_prepare() {
+  if constexpr (plane_fits<R, NX>()) {
+    constexpr int NT = plane_threads(NX);
+    cudaError_t e = cudaFuncSetAttribute(k_pass1_assemble_ifft_xy<R, NX, NX, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<R, NX>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pass3_fft_xy_project<R, NX, NX, NT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<R, NX>());
+    return e;
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R, int N3>
+static cudaError_t z_prepare() {
+  constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
+  constexpr int NT = z_threads(N3);
+  return cudaFuncSetAttribute(k_pass2_z_material<R, N3, TX, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)z_smem<R, N3>());
+}
+
+template <typename R, int NX>
+static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
+  if constexpr (plane_fits<R, NX>()) {
+    constexpr int NT = plane_threads(NX);
+    dim3 grid(3, 2, a.n3);
+    if (which == 1) {
+      k_pass1_assemble_ifft_xy<R, NX, NX, NT><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
+          a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip);
+    } else {
+      k_pass3_fft_xy_project<R, NX, NX, NT><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
+          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip);
+    }
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R, int N3>
+static cudaError_t z_launch(const MatvecArgs<R>& a) {
+  constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
+  constexpr int NT = z_threads(N3);
+  const int ncols = a.n1 * a.n2;
+  MatView<R> mv{a.inv_phi, a.gam, a.inv_mu, a.kind, a.ax_a, a.ax_b, (long long)ncols * a.n3};
+  const R inv_n = (R)(1.0 / ((double)ncols * (double)a.n3));
+  k_pass2_z_material<R, N3, TX, NT><<<ncols / TX, NT, z_smem<R, N3>(), a.stream>>>(a.fld, mv, a.tw3, ncols, inv_n,
+                                                                                 a.skip);
+  return cudaGetLastError();
+}
+
+static inline bool size_ok(int n) {
+  switch (n) {
+    case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: return true;
+    default: return false;
+  }
+}
+
+template <typename R>
+static bool plane_fits_rt(int n) {
+  switch (n) {
+#define NFS_CASE(N) case N: return plane_fits<R, N>();
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+    default: return false;
+  }
+}
+
+template <typename R>
+static int z_tile_rt(int n3) { return z_tile(n3, (int)sizeof(cplx<R>)); }
+
+template <typename R>
+bool matvec_supported(int n1, int n2, int n3) {
+  if (n1 != n2 || !size_ok(n1) || !size_ok(n3)) return false;
+  if (!plane_fits_rt<R>(n1)) return false;
+  if ((n1 * n2) % z_tile_rt<R>(n3) != 0) return false;
+  return true;
+}
+
+template <typename R>
+cudaError_t matvec_prepare(int n1, int n2, int n3) {
+  if (!matvec_supported<R>(n1, n2, n3)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (n1) {
+#define NFS_CASE(N) case N: e = plane_prepare<R, N>(); break;
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  if (e != cudaSuccess) return e;
+  switch (n3) {
+#define NFS_CASE(N) case N: e = z_prepare<R, N>(); break;
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return e;
+}
+
+template <typename R>
+static cudaError_t plane_dispatch(const MatvecArgs<R>& a, int which) {
+  switch (a.n1) {
+#define NFS_CASE(N) case N: return plane_launch<R, N>(a, which);
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+static cudaError_t z_dispatch(const MatvecArgs<R>& a) {
+  switch (a.n3) {
+#define NFS_CASE(N) case N: return z_launch<R, N>(a);
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+cudaError_t matvec_launch(const MatvecArgs<R>& a) {
+  cudaError_t e = plane_dispatch<R>(a, 1);
+  if (e != cudaSuccess) return e;
+  e = z_dispatch<R>(a);
+  if (e != cudaSuccess) return e;
+  return plane_dispatch<R>(a, 3);
+}
+
+template <typename R>
+cudaError_t matvec_launch_mask(const MatvecArgs<R>& a, int mask) {
+  cudaError_t e = cudaSuccess;
+  if (mask & 1) e = plane_dispatch<R>(a, 1);
+  if (e == cudaSuccess && (mask & 2)) e = z_dispatch<R>(a);
+  if (e == cudaSuccess && (mask & 4)) e = plane_dispatch<R>(a, 3);
+  return e;
+}
+
+template <typename R>
+cudaError_t pass1_launch(const MatvecArgs<R>& a) {
+  return plane_dispatch<R>(a, 1);
+}
+
+#define NFS_INSTANTIATE_MATVEC(R)                                            \
+  template bool matvec_supported<R>(int, int, int);                        \
+  template cudaError_t matvec_prepare<R>(int, int, int);                   \
+  template cudaError_t matvec_launch<R>(const MatvecArgs<R>&);             \
+  template cudaError_t matvec_launch_mask<R>(const MatvecArgs<R>&, int);   \
+  template cudaError_t pass1_launch<R>(const MatvecArgs<R>&);
+
+}  // namespace nfs

@@ -1,0 +1,295 @@
+// The A_r matrix-vector product of the HHPD-NFGEP (eq. factor_mtx, applied
+// as in eq. spd_LS) in three HBM passes:
+//
+//   pass 1  (cluster of 3 CTAs per (z-plane i3, group)):  spectral assembly
+//           p^ = P_r-coefficients, q^ = Q_r-coefficients per voxel, then the
+//           inverse DFT along x and y.  Group 0 builds p = P_r [u1a; u1b],
+//           group 1 builds q = Q_r [u2a; u2b]; CTA rank c owns component c.
+//   pass 2  (one CTA per tile of xy columns):  inverse DFT along z, the
+//           per-voxel material product of eq. factor_mtx, forward DFT along z.
+//   pass 3  (cluster of 3 CTAs per (z-plane, group)):  forward DFT along y
+//           and x, then the projections P_r^* f (group 0) or Q_r^* w (group 1).
+//
+// Basis per spectral voxel (Section 2), with a = (Lambda_1, Lambda_2, Lambda_3),
+// t = (alpha, beta, 1), Lambda_p = t x a, Lambda_q = |a|^2:
+//   c  = Lambda_p / |Lambda_p|                  (= conj Pi_2, eq. mtx_Pi_2)
+//   x  = (a / sqrt(Lambda_q)) x conj(c)          (= Pi_0 x Pi_2 = conj Pi_1)
+// so that P_r = (I3 (x) T)[-c, x] and Q_r = (I3 (x) T)[conj x, conj c]
+// (eq. mtx_QdPd, SVD theorem thm:svd_C).  x equals conj(Pi_1) because
+// Pi_1 = (conj(a) x Lambda_p) / sqrt(Lambda_q |Lambda_p|^2), the unit-norm
+// reading of eq. mtx_Pi_1.
+//
+// The Bloch twist D of T (eq. mtx_T) is a per-voxel unit scalar and commutes
+// with the per-voxel material product, so it cancels between T and T^*: the
+// kernels run plain DFTs.  The two unnormalised DFTs give a factor n, removed
+// in pass 2 (T = D U / sqrt(n)).
+//
+// Field buffer layout: fld[g][c][i3][j2][j1], g in {p/f, q/w}, c in {x, y, z};
+// z is spectral in passes 1 -> 2 and 2 -> 3, x and y are real-space.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "fft_smem.cuh"
+
+namespace nfs {
+namespace cg = cooperative_groups;
+
+constexpr int kMediumChiral = 0;
+constexpr int kMediumPseudochiral = 1;
+
+// Per-voxel real-space material (Section 4.3 with diagonal eps and mu):
+//   inv_phi[3][n] = 1 / Phi_c, Phi = eps - xi mu^{-1} zeta (diagonal here)
+//   gam     chiral [3][n] gamma_c; pseudochiral [n] gamma
+//   inv_mu  [3][n] = 1 / mu_c, or nullptr for mu = 1
+template <typename R>
+struct MatView {
+  const R* inv_phi;
+  const R* gam;
+  const R* inv_mu;
+  int kind;
+  int ax_a, ax_b;
+  long long n;
+};
+
+template <typename R>
+struct Basis {
+  cplx<R> c[3];
+  cplx<R> x[3];
+};
+
+template <typename R>
+__device__ __forceinline__ void make_basis(cplx<R> a1, cplx<R> a2, cplx<R> a3, R al, R be, Basis<R>& B) {
+  using C = cplx<R>;
+  // Lambda_p = t x a  (eq. mtx_Lambda_p_q)
+  const C p1 = mk(be * a3.x - a2.x, be * a3.y - a2.y);
+  const C p2 = mk(a1.x - al * a3.x, a1.y - al * a3.y);
+  const C p3 = mk(al * a2.x - be * a1.x, al * a2.y - be * a1.y);
+  const R lp2 = cabs2(p1) + cabs2(p2) + cabs2(p3);
+  const R lq = cabs2(a1) + cabs2(a2) + cabs2(a3);
+  const R rp = rsqrt(lp2);
+  const R rq = rsqrt(lq);
+  B.c[0] = cscale(p1, rp);
+  B.c[1] = cscale(p2, rp);
+  B.c[2] = cscale(p3, rp);
+  // x = (a / sqrt(Lq)) x conj(c):  x_1 = a2 conj(c3) - a3 conj(c2), cyclic
+  B.x[0] = cscale(csub(cmulc(B.c[2], a2), cmulc(B.c[1], a3)), rq);
+  B.x[1] = cscale(csub(cmulc(B.c[0], a3), cmulc(B.c[2], a1)), rq);
+  B.x[2] = cscale(csub(cmulc(B.c[1], a1), cmulc(B.c[0], a2)), rq);
+}
+
+// ---------------------------------------------------------------------------
+// pass 1
+// ---------------------------------------------------------------------------
+template <typename R, int NX, int NY, int NT>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT)
+k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fld,
+                         const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
+                         const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
+                         const int* __restrict__ skip) {
+  using C = cplx<R>;
+  constexpr int PITCH = NX + 1;
+  constexpr int NE = NX * NY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* plane = reinterpret_cast<C*>(smem_raw);
+  C* stx = plane + NY * PITCH;
+  C* sty = stx + NX;
+  cg::cluster_group cl = cg::this_cluster();
+  if (skip != nullptr && *skip) return;  // uniform across the grid
+  const int rank = (int)cl.block_rank();
+  const int grp = blockIdx.y;
+  const int i3 = blockIdx.z;
+  for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
+  for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
+
+  const long long n = (long long)NE * n3;
+  const C* ua = u + (2 * grp) * n + (long long)i3 * NE;
+  const C* ub = ua + n;
+  const C a3 = lam[NX + NY + i3];
+  C* dst0 = cl.map_shared_rank(plane, 0);
+  C* dst1 = cl.map_shared_rank(plane, 1);
+  C* dst2 = cl.map_shared_rank(plane, 2);
+  cl.sync();  // every CTA of the cluster is resident before remote stores
+
+  const int e0 = (rank * NE) / 3, e1 = ((rank + 1) * NE) / 3;
+  for (int e = e0 + threadIdx.x; e < e1; e += NT) {
+    const int i1 = e % NX, i2 = e / NX;
+    Basis<R> B;
+    make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
+    const C va = ua[e], vb = ub[e];
+    C o[3];
+    if (grp == 0) {
+      // p^ = -c u1a + x u1b
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o[k] = csub(cmul(B.x[k], vb), cmul(B.c[k], va));
+    } else {
+      // q^ = conj(x) u2a + conj(c) u2b
+#pragma unroll
+      for (int k = 0; k < 3; ++k) o[k] = cadd(cmulc(B.x[k], va), cmulc(B.c[k], vb));
+    }
+    const int s = i2 * PITCH + i1;
+    dst0[s] = o[0];
+    dst1[s] = o[1];
+    dst2[s] = o[2];
+  }
+  cl.sync();
+  smem_fft<true, NX, NY, NT, PITCH, 1>(plane, stx);  // along x (rows)
+  smem_fft<true, NY, NX, NT, 1, PITCH>(plane, sty);  // along y (columns)
+  C* out = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
+  for (int e = threadIdx.x; e < NE; e += NT) out[e] = plane[(e / NX) * PITCH + (e % NX)];
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: the material product of eq. factor_mtx, per real-space voxel:
+//   w = Phi^{-1} (xi mu^{-1} p + q),   f = mu^{-1} (zeta w + p)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void material_apply(const MatView<R>& m, long long v, const cplx<R>* p,
+                                               const cplx<R>* q, cplx<R>* f, cplx<R>* w, R scale) {
+  using C = cplx<R>;
+  R ip[3], im[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    ip[c] = m.inv_phi[c * m.n + v];
+    im[c] = m.inv_mu ? m.inv_mu[c * m.n + v] : (R)1;
+  }
+  if (m.kind == kMediumChiral) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const R g = m.gam[c * m.n + v];
+      // xi mu^{-1} p = i g im p;  w = ip (q + i g im p)
+      const R gi = g * im[c];
+      const C s = mk(q[c].x - gi * p[c].y, q[c].y + gi * p[c].x);
+      const C wc = cscale(s, ip[c]);
+      // zeta w = -i g w;  f = im (p - i g w)
+      const C fc = mk(p[c].x + g * wc.y, p[c].y - g * wc.x);
+      w[c] = cscale(wc, scale);
+      f[c] = cscale(fc, im[c] * scale);
+    }
+  } else {
+    const R g = m.gam[v];
+    const int a = m.ax_a, b = m.ax_b;
+    C xmp[3] = {mk((R)0, (R)0), mk((R)0, (R)0), mk((R)0, (R)0)};
+    // (xi mu^{-1} p)_a = i g im_b p_b ; (.)_b = i g im_a p_a
+    xmp[a] = cmul_i(cscale(p[b], g * im[b]));
+    xmp[b] = cmul_i(cscale(p[a], g * im[a]));
+    C wc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) wc[c] = cscale(cadd(q[c], xmp[c]), ip[c]);
+    C zw[3] = {mk((R)0, (R)0), mk((R)0, (R)0), mk((R)0, (R)0)};
+    // (zeta w)_a = -i g w_b ; (.)_b = -i g w_a
+    zw[a] = cmul_mi(cscale(wc[b], g));
+    zw[b] = cmul_mi(cscale(wc[a], g));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w[c] = cscale(wc[c], scale);
+      f[c] = cscale(cadd(p[c], zw[c]), im[c] * scale);
+    }
+  }
+}
+
+template <typename R, int N3, int TX, int NT>
+__global__ void __launch_bounds__(NT)
+k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __restrict__ twz, int ncols,
+                   R inv_n, const int* __restrict__ skip) {
+  using C = cplx<R>;
+  constexpr int LINES = 6 * TX;
+  constexpr int PITCH = LINES + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* stw = buf + N3 * PITCH;
+  if (skip != nullptr && *skip) return;
+  for (int i = threadIdx.x; i < N3; i += NT) stw[i] = twz[i];
+  const int col0 = blockIdx.x * TX;
+  const long long n = (long long)ncols * N3;
+  for (int idx = threadIdx.x; idx < N3 * LINES; idx += NT) {
+    const int c = idx % TX;
+    const int t = idx / TX;
+    const int f = t % 6, z = t / 6;
+    buf[z * PITCH + f * TX + c] = fld[f * n + (long long)z * ncols + col0 + c];
+  }
+  __syncthreads();
+  smem_fft<true, N3, LINES, NT, 1, PITCH>(buf, stw);
+  for (int idx = threadIdx.x; idx < N3 * TX; idx += NT) {
+    const int c = idx % TX, z = idx / TX;
+    C* row = buf + z * PITCH + c;
+    C p[3] = {row[0], row[TX], row[2 * TX]};
+    C q[3] = {row[3 * TX], row[4 * TX], row[5 * TX]};
+    C fo[3], wo[3];
+    material_apply<R>(mat, (long long)z * ncols + col0 + c, p, q, fo, wo, inv_n);
+    row[0] = fo[0];
+    row[TX] = fo[1];
+    row[2 * TX] = fo[2];
+    row[3 * TX] = wo[0];
+    row[4 * TX] = wo[1];
+    row[5 * TX] = wo[2];
+  }
+  __syncthreads();
+  smem_fft<false, N3, LINES, NT, 1, PITCH>(buf, stw);
+  for (int idx = threadIdx.x; idx < N3 * LINES; idx += NT) {
+    const int c = idx % TX;
+    const int t = idx / TX;
+    const int f = t % 6, z = t / 6;
+    fld[f * n + (long long)z * ncols + col0 + c] = buf[z * PITCH + f * TX + c];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 3
+// ---------------------------------------------------------------------------
+template <typename R, int NX, int NY, int NT>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT)
+k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au,
+                       const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
+                       const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
+                       const int* __restrict__ skip) {
+  using C = cplx<R>;
+  constexpr int PITCH = NX + 1;
+  constexpr int NE = NX * NY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* plane = reinterpret_cast<C*>(smem_raw);
+  C* stx = plane + NY * PITCH;
+  C* sty = stx + NX;
+  cg::cluster_group cl = cg::this_cluster();
+  if (skip != nullptr && *skip) return;
+  const int rank = (int)cl.block_rank();
+  const int grp = blockIdx.y;
+  const int i3 = blockIdx.z;
+  for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
+  for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
+  const C* in = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
+  for (int e = threadIdx.x; e < NE; e += NT) plane[(e / NX) * PITCH + (e % NX)] = in[e];
+  __syncthreads();
+  smem_fft<false, NX, NY, NT, PITCH, 1>(plane, stx);
+  smem_fft<false, NY, NX, NT, 1, PITCH>(plane, sty);
+  cl.sync();
+  const C* src0 = cl.map_shared_rank(plane, 0);
+  const C* src1 = cl.map_shared_rank(plane, 1);
+  const C* src2 = cl.map_shared_rank(plane, 2);
+  const long long n = (long long)NE * n3;
+  C* o0 = Au + (2 * grp) * n + (long long)i3 * NE;
+  C* o1 = o0 + n;
+  const C a3 = lam[NX + NY + i3];
+  const int e0 = (rank * NE) / 3, e1 = ((rank + 1) * NE) / 3;
+  for (int e = e0 + threadIdx.x; e < e1; e += NT) {
+    const int i1 = e % NX, i2 = e / NX;
+    const int s = i2 * PITCH + i1;
+    const C f[3] = {src0[s], src1[s], src2[s]};
+    Basis<R> B;
+    make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
+    C r0, r1;
+    if (grp == 0) {
+      // P_r^* f = [-sum conj(c) f ; sum conj(x) f]
+      r0 = cneg(cadd(cadd(cmulc(B.c[0], f[0]), cmulc(B.c[1], f[1])), cmulc(B.c[2], f[2])));
+      r1 = cadd(cadd(cmulc(B.x[0], f[0]), cmulc(B.x[1], f[1])), cmulc(B.x[2], f[2]));
+    } else {
+      // Q_r^* w = [sum x w ; sum c w]
+      r0 = cadd(cadd(cmul(B.x[0], f[0]), cmul(B.x[1], f[1])), cmul(B.x[2], f[2]));
+      r1 = cadd(cadd(cmul(B.c[0], f[0]), cmul(B.c[1], f[1])), cmul(B.c[2], f[2]));
+    }
+    o0[e] = r0;
+    o1[e] = r1;
+  }
+  cl.sync();  // keep this CTA's plane alive until the cluster finished reading it
+}
+
+}  // namespace nfs

@@ -1,0 +1,45 @@
+// Complex arithmetic on CUDA vector types (float2 / double2), used by every
+// kernel of libnfs.  Element type C is float2 (complex64) or double2
+// (complex128); R is the matching real type.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace nfs {
+
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+template <typename R> using cplx = typename CplxOf<R>::type;
+
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { using type = float; };
+template <> struct RealOf<double2> { using type = double; };
+
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __host__ __device__ __forceinline__ C cneg(C a) { return mk(-a.x, -a.y); }
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+// a * b
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc + a * b
+template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C acc) {
+  return mk(acc.x + a.x * b.x - a.y * b.y, acc.y + a.x * b.y + a.y * b.x);
+}
+// i * a, -i * a
+template <typename C> __host__ __device__ __forceinline__ C cmul_i(C a) { return mk(-a.y, a.x); }
+template <typename C> __host__ __device__ __forceinline__ C cmul_mi(C a) { return mk(a.y, -a.x); }
+template <typename C> __host__ __device__ __forceinline__ typename RealOf<C>::type cabs2(C a) {
+  return a.x * a.x + a.y * a.y;
+}
+
+}  // namespace nfs

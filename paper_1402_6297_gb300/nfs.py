@@ -1,0 +1,323 @@
+"""ctypes binding of libnfs (include/nfs.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library.  PyTorch supplies device
+memory and the stream; tensors crossing the boundary are CUDA tensors of
+dtype complex128 (NFS_C128) or complex64 (NFS_C64), 4n elements, laid out
+[u1a | u1b | u2a | u2b] in spectral order (see the header).
+
+If the library has not been built the first call raises ``NFSLibraryMissing``;
+there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libnfs.so")
+
+NFS_OK = 0
+NFS_EINVAL = -1
+NFS_EUNSUPPORTED = -2
+NFS_EKPOINT = -3
+NFS_EBASIS = -4
+NFS_ENOTHPD = -5
+NFS_ENOCONV = -6
+NFS_EBREAKDOWN = -7
+NFS_ETIMEOUT = -8
+NFS_ECUDA = -9
+NFS_ENOMEM = -10
+
+MEDIUM_CHIRAL = 0
+MEDIUM_PSEUDOCHIRAL = 1
+PREC_FP64 = 0
+PREC_MIXED = 1
+C128 = 0
+C64 = 1
+
+EXPORTED = (
+    "nfs_default_options", "nfs_setup", "nfs_matvec", "nfs_matvec_passes", "nfs_apply_Br", "nfs_cg_solve",
+    "nfs_eigs", "nfs_eig_grad", "nfs_num_voxels", "nfs_device_bytes", "nfs_set_stream",
+    "nfs_destroy", "nfs_strerror",
+)
+
+
+class NFSLibraryMissing(RuntimeError):
+    pass
+
+
+class NFSError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {_strerror(code)} (code {code})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("cg_tol", ctypes.c_double),
+        ("cg_maxit", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("max_refine", ctypes.c_int),
+        ("eig_tol", ctypes.c_double),
+        ("ncv", ctypes.c_int),
+        ("max_restarts", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("axis_a", ctypes.c_int),
+        ("axis_b", ctypes.c_int),
+        ("eps", ctypes.POINTER(ctypes.c_double)),
+        ("mu", ctypes.POINTER(ctypes.c_double)),
+        ("gamma", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int),
+        ("refinements", ctypes.c_int),
+        ("rel_residual", ctypes.c_double),
+        ("status", ctypes.c_int),
+    ]
+
+
+class EigsInfo(ctypes.Structure):
+    _fields_ = [
+        ("lanczos_steps", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("cg_iterations", ctypes.c_longlong),
+        ("matvecs_c64", ctypes.c_longlong),
+        ("matvecs_c128", ctypes.c_longlong),
+        ("nconv", ctypes.c_int),
+        ("max_ritz_residual", ctypes.c_double),
+        ("status", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libnfs.so (once).  Raises NFSLibraryMissing if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise NFSLibraryMissing(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.nfs_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.nfs_default_options.restype = None
+    L.nfs_setup.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Material), ctypes.POINTER(Options)]
+    L.nfs_setup.restype = ip
+    L.nfs_matvec.argtypes = [vp, ip, vp, vp]
+    L.nfs_matvec.restype = ip
+    L.nfs_matvec_passes.argtypes = [vp, ip, ip, vp, vp]
+    L.nfs_matvec_passes.restype = ip
+    L.nfs_apply_Br.argtypes = [vp, vp, vp]
+    L.nfs_apply_Br.restype = ip
+    L.nfs_cg_solve.argtypes = [vp, vp, vp, ctypes.POINTER(SolveInfo)]
+    L.nfs_cg_solve.restype = ip
+    L.nfs_eigs.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(EigsInfo)]
+    L.nfs_eigs.restype = ip
+    L.nfs_eig_grad.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, vp, vp]
+    L.nfs_eig_grad.restype = ip
+    L.nfs_num_voxels.argtypes = [vp]
+    L.nfs_num_voxels.restype = ctypes.c_longlong
+    L.nfs_device_bytes.argtypes = [vp]
+    L.nfs_device_bytes.restype = ctypes.c_longlong
+    L.nfs_set_stream.argtypes = [vp, vp]
+    L.nfs_set_stream.restype = ip
+    L.nfs_destroy.argtypes = [vp]
+    L.nfs_destroy.restype = None
+    L.nfs_strerror.argtypes = [ip]
+    L.nfs_strerror.restype = ctypes.c_char_p
+    _ = dp
+    _lib = L
+    return L
+
+
+def _strerror(code):
+    try:
+        return lib().nfs_strerror(int(code)).decode()
+    except NFSLibraryMissing:
+        return "libnfs missing"
+
+
+def _check(code, where):
+    if code != NFS_OK:
+        raise NFSError(code, where)
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().nfs_default_options(ctypes.byref(o))
+    return o
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One Bloch problem on the GPU: grid, k, medium, options (nfs_setup)."""
+
+    def __init__(self, grid, kdota, medium, precision="fp64", stream=None, **opts):
+        import torch  # device memory and streams
+        L = lib()
+        self.grid = tuple(int(g) for g in grid)
+        n1, n2, n3 = self.grid
+        self.n = n1 * n2 * n3
+        self.N = 4 * self.n
+        self.medium = medium
+        o = default_options()
+        o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        for key, val in opts.items():
+            setattr(o, key, val)
+        self.stream_handle = stream if stream is not None else _current_stream()
+        o.stream = self.stream_handle
+        self.options = o
+        self.precision = precision
+        eps = np.ascontiguousarray(medium.eps, dtype=np.float64)
+        gam = np.ascontiguousarray(medium.gamma, dtype=np.float64)
+        mu = None if medium.mu is None else np.ascontiguousarray(medium.mu, dtype=np.float64)
+        m = Material()
+        m.kind = MEDIUM_CHIRAL if medium.kind == "chiral" else MEDIUM_PSEUDOCHIRAL
+        m.axis_a, m.axis_b = (int(medium.axes[0]), int(medium.axes[1]))
+        m.eps = _dptr(eps)
+        m.gamma = _dptr(gam)
+        m.mu = _dptr(mu) if mu is not None else ctypes.POINTER(ctypes.c_double)()
+        self._keep = (eps, gam, mu)
+        a = float(getattr(medium, "a", 1.0))
+        lattice = np.diag([a, a, a]).astype(np.float64).ravel()
+        # kdota = (k.a_1, k.a_2, k.a_3); for a lattice a_l = a e_l, k = kdota / a
+        kvec = np.asarray(kdota, dtype=np.float64) / a
+        g = (ctypes.c_int * 3)(*self.grid)
+        h = ctypes.c_void_p()
+        _check(L.nfs_setup(ctypes.byref(h), g, _dptr(lattice), _dptr(kvec), ctypes.byref(m), ctypes.byref(o)),
+               "nfs_setup")
+        self.h = h
+        self._torch = torch
+
+    # -- helpers --------------------------------------------------------------
+    def _vec(self, t, dtype):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+                and t.numel() == self.N):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {self.N} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nfs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def device_bytes(self):
+        return int(lib().nfs_device_bytes(self.h))
+
+    # -- operations -----------------------------------------------------------
+    def matvec(self, u, out=None):
+        """A_r u (complex128 or complex64 CUDA tensor)."""
+        torch = self._torch
+        dt = u.dtype
+        code = C128 if dt == torch.complex128 else C64
+        if out is None:
+            out = torch.empty_like(u)
+        _check(lib().nfs_matvec(self.h, code, self._vec(u, dt), self._vec(out, dt)), "nfs_matvec")
+        return out
+
+    def matvec_passes(self, mask, u, out):
+        """Only the selected passes of the product (timing aid; see nfs.h)."""
+        torch = self._torch
+        dt = u.dtype
+        code = C128 if dt == torch.complex128 else C64
+        _check(lib().nfs_matvec_passes(self.h, code, int(mask), self._vec(u, dt), self._vec(out, dt)),
+               "nfs_matvec_passes")
+        return out
+
+    def apply_Br(self, v, out=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty_like(v)
+        _check(lib().nfs_apply_Br(self.h, self._vec(v, torch.complex128), self._vec(out, torch.complex128)),
+               "nfs_apply_Br")
+        return out
+
+    def cg_solve(self, b, x0=None):
+        torch = self._torch
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        info = SolveInfo()
+        code = lib().nfs_cg_solve(self.h, self._vec(b, torch.complex128), self._vec(x, torch.complex128),
+                                  ctypes.byref(info))
+        if code not in (NFS_OK, NFS_ENOCONV):
+            raise NFSError(code, "nfs_cg_solve")
+        return x, info
+
+    def eigs(self, nev, vectors=True, allow_noconv=False):
+        torch = self._torch
+        omega = np.zeros(nev, dtype=np.float64)
+        Y = torch.empty((nev, self.N), dtype=torch.complex128, device="cuda") if vectors else None
+        info = EigsInfo()
+        code = lib().nfs_eigs(self.h, int(nev), _dptr(omega), ctypes.c_void_p(Y.data_ptr()) if vectors else None,
+                              ctypes.byref(info))
+        if code != NFS_OK and not (allow_noconv and code == NFS_ENOCONV):
+            raise NFSError(code, "nfs_eigs")
+        return omega, Y, info
+
+    def eig_grad(self, Y, weights):
+        """d(sum_j w_j omega_j) / d(per-component eps, gamma) from eigenvectors Y."""
+        torch = self._torch
+        m = int(Y.shape[0])
+        if not (Y.is_cuda and Y.dtype == torch.complex128 and Y.is_contiguous() and Y.shape[1] == self.N):
+            raise ValueError("Y must be a contiguous CUDA complex128 tensor (m, 4n)")
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(m))
+        n1, n2, n3 = self.grid
+        d_eps = torch.empty((3, n3, n2, n1), dtype=torch.float64, device="cuda")
+        gshape = (3, n3, n2, n1) if self.medium.kind == "chiral" else (n3, n2, n1)
+        d_gam = torch.empty(gshape, dtype=torch.float64, device="cuda")
+        _check(lib().nfs_eig_grad(self.h, m, _dptr(w), ctypes.c_void_p(Y.data_ptr()),
+                                  ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_gam.data_ptr())),
+               "nfs_eig_grad")
+        return d_eps, d_gam
+
+
+def residuals(ctx: Context, omega, Y):
+    """||A_r y - omega B_r y|| / ||y|| per eigenpair (FP64, through the ABI)."""
+    out = []
+    for j in range(len(omega)):
+        y = Y[j].contiguous()
+        r = ctx.matvec(y) - float(omega[j]) * ctx.apply_Br(y)
+        out.append(float(r.norm() / y.norm()))
+    return out

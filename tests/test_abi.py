@@ -1,0 +1,133 @@
+"""The C-ABI library builds, loads and exports every symbol include/nfs.h
+declares; struct layouts agree with the binding; host-side validation returns
+the documented error codes (these checks run before any CUDA call, so they
+need no GPU)."""
+
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nfs.h")
+
+
+@pytest.fixture(scope="module")
+def nfs():
+    from paper_1402_6297_gb300 import build, nfs as binding
+    build.build()
+    binding.lib()
+    return binding
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nfs_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(nfs):
+    names = declared_functions()
+    assert len(names) >= 12
+    L = nfs.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(nfs.EXPORTED) | (set(names) - set(nfs.EXPORTED))
+    for name in nfs.EXPORTED:
+        assert name in names
+
+
+def test_struct_layouts_match_header(nfs):
+    src = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "nfs.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(nfs_options), sizeof(nfs_material), sizeof(nfs_solve_info), sizeof(nfs_eigs_info));
+  printf("%zu %zu %zu\n", offsetof(nfs_options, seed), offsetof(nfs_options, stream), offsetof(nfs_eigs_info, max_ritz_residual));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = subprocess.check_output([exe]).decode().split()
+    sizes = list(map(int, out))
+    assert sizes[0] == ctypes.sizeof(nfs.Options)
+    assert sizes[1] == ctypes.sizeof(nfs.Material)
+    assert sizes[2] == ctypes.sizeof(nfs.SolveInfo)
+    assert sizes[3] == ctypes.sizeof(nfs.EigsInfo)
+    assert sizes[4] == nfs.Options.seed.offset
+    assert sizes[5] == nfs.Options.stream.offset
+    assert sizes[6] == nfs.EigsInfo.max_ritz_residual.offset
+
+
+def test_default_options(nfs):
+    o = nfs.default_options()
+    assert o.precision == nfs.PREC_FP64
+    assert (o.alpha, o.beta) == (2.0, 3.0)
+    assert o.cg_tol == 1e-12 and o.eig_tol == 1e-10
+    assert nfs.lib().nfs_strerror(nfs.NFS_EKPOINT).decode().startswith("k.a_l")
+
+
+def _setup(nfs, grid, k, med, **opt):
+    L = nfs.lib()
+    o = nfs.default_options()
+    for key, v in opt.items():
+        setattr(o, key, v)
+    m = nfs.Material()
+    m.kind = 0 if med.kind == "chiral" else 1
+    m.axis_a, m.axis_b = med.axes
+    eps = np.ascontiguousarray(med.eps)
+    gam = np.ascontiguousarray(med.gamma)
+    m.eps = eps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    m.gamma = gam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    m.mu = ctypes.POINTER(ctypes.c_double)()
+    h = ctypes.c_void_p()
+    g = (ctypes.c_int * 3)(*grid)
+    kk = np.asarray(k, dtype=np.float64)
+    code = L.nfs_setup(ctypes.byref(h), g, None, kk.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       ctypes.byref(m), ctypes.byref(o))
+    assert not h.value  # these cases never create a context
+    return code
+
+
+def test_validation_errors_without_gpu(nfs):
+    g = (8, 8, 8)
+    med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+    # Lemma: k = 0 (all k.a_l integer) makes Lambda_q singular
+    assert _setup(nfs, g, (0.0, 0.0, 0.0), med) == nfs.NFS_EKPOINT
+    assert _setup(nfs, g, (1.0, 0.0, 2.0), med) == nfs.NFS_EKPOINT
+    # Lemma: alpha dx = beta dy with k1 = k2 = k3 gives Lambda_p = 0 somewhere
+    assert _setup(nfs, g, (0.2, 0.2, 0.2), med, alpha=1.0, beta=1.0) == nfs.NFS_EBASIS
+    assert _setup(nfs, g, (0.1, 0.2, 0.3), med, alpha=0.0) == nfs.NFS_EBASIS
+    # Assumption: Phi = eps - gamma^2 must stay positive
+    bad = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 3.7)
+    assert _setup(nfs, g, (0.1, 0.2, 0.3), bad) == nfs.NFS_ENOTHPD
+    neg = wl.homogeneous(g, eps=-1.0)
+    assert _setup(nfs, g, (0.1, 0.2, 0.3), neg) == nfs.NFS_ENOTHPD
+    # unsupported sizes and shapes
+    assert _setup(nfs, (10, 10, 10), (0.1, 0.2, 0.3), wl.homogeneous((10, 10, 10))) == nfs.NFS_EUNSUPPORTED
+    assert _setup(nfs, (8, 16, 8), (0.1, 0.2, 0.3), wl.homogeneous((8, 16, 8))) == nfs.NFS_EUNSUPPORTED
+    # bad options
+    assert _setup(nfs, g, (0.1, 0.2, 0.3), med, precision=7) == nfs.NFS_EINVAL
+    assert _setup(nfs, g, (0.1, 0.2, 0.3), med, cg_tol=0.0) == nfs.NFS_EINVAL
+    pc = wl.pseudochiral_cylinders(g, axes=(1, 1))
+    assert _setup(nfs, g, (0.1, 0.2, 0.3), pc) == nfs.NFS_EINVAL
+
+
+def test_null_handles_rejected(nfs):
+    L = nfs.lib()
+    assert L.nfs_matvec(None, 0, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_cg_solve(None, None, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_eigs(None, 3, None, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_eig_grad(None, 1, None, None, None, None) == nfs.NFS_EINVAL
+    L.nfs_destroy(None)

@@ -13,7 +13,7 @@ Conventions (shared by every consumer):
   says coefficients are averaged over neighbouring grid points; this module
   fixes one concrete discretisation and every consumer uses the same arrays.
 * ``kdota`` is the triple (k . a_1, k . a_2, k . a_3): the Bloch phase across
-  one lattice vector a_l is exp(i 2 pi k . a_l) (Eq. (1.2)).
+  one lattice vector a_l is exp(i 2 pi k . a_l) (eq. (quasi_periodic)).
 
 A :class:`Medium` is a plain record of per-component real arrays:
 
