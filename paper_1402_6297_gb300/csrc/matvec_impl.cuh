@@ -13,7 +13,7 @@ __host__ __device__ constexpr int plane_threads(int N) {
 }
 // xy columns per CTA of the z pass, per z length and element size.
 __host__ __device__ constexpr int z_tile(int N3, int csize) {
-  return N3 <= 24 ? 32 : ((csize == 16 && N3 >= 96) ? 8 : 16);
+  return (csize == 16 && N3 >= 96) ? 8 : 16;
 }
 __host__ __device__ constexpr int z_threads(int N3) { return N3 == 128 ? 512 : 384; }
 
