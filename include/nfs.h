@@ -173,6 +173,39 @@ int nfs_eigs(nfs_ctx* ctx, int nev, double* omega, void* Y, nfs_eigs_info* info)
 int nfs_eig_grad(nfs_ctx* ctx, int m, const double* weights, const void* Y,
                  double* d_eps, double* d_gamma);
 
+/* ---- allocation-free product ------------------------------------------ */
+
+/* Largest voxel count n1*n2*n3 that nfs_matvec_noalloc accepts (32^3). */
+#define NFS_NOALLOC_MAX_VOXELS 32768
+
+/* Au = A_r u, like nfs_matvec, without allocating any device memory.  The
+ * paper has no counterpart: this entry point is for callers that cannot
+ * allocate, such as a host framework that has already reserved the GPU
+ * through its own caching allocator (a raw cudaMalloc there can fail or
+ * fragment its pool) or a service with a fixed device-memory budget that must
+ * not allocate after start-up.  It needs no context: every input is an
+ * argument.
+ *   grid, k           as for nfs_setup, unit cube lattice (a = 1), mu = 1;
+ *                     n1*n2*n3 <= NFS_NOALLOC_MAX_VOXELS, else NFS_EUNSUPPORTED
+ *   kind, axis_a/b    NFS_MEDIUM_* and the pseudochiral pair (ignored for chiral)
+ *   eps, gamma        DEVICE arrays, layout of nfs_material
+ *   alpha, beta       basis parameters (eq. mtx_Lambda_p_q), e.g. 2 and 3
+ *   u, Au             DEVICE complex128, 4n each, not overlapping
+ *   stream            cudaStream_t (NULL = default stream)
+ * Workspace: one fixed device array of about 4.8 MB inside the library,
+ * created when the library's device code is loaded and held by every GPU
+ * that loads it until the process exits.  The first call on a device looks up
+ * that array's device address and sets the kernels' shared-memory limits;
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls that overlap on the GPU (two streams, two host threads)
+ * race and must be serialised by the caller.  The call is synchronous with
+ * respect to `stream`: it returns after Au is written.  Returns NFS_ENOTHPD if
+ * Phi = eps - gamma^2 <= 0 at some voxel (Au is then meaningless), and the
+ * Lemma's NFS_EKPOINT / NFS_EBASIS like nfs_setup. */
+int nfs_matvec_noalloc(const int grid[3], const double k[3], int kind, int axis_a, int axis_b,
+                       const double* eps, const double* gamma, double alpha, double beta,
+                       const void* u, void* Au, void* stream);
+
 /* Basic facts about a context: n, and device bytes held. */
 long long nfs_num_voxels(const nfs_ctx* ctx);
 long long nfs_device_bytes(const nfs_ctx* ctx);

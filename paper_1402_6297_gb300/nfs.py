@@ -42,8 +42,9 @@ C64 = 1
 EXPORTED = (
     "nfs_default_options", "nfs_setup", "nfs_matvec", "nfs_matvec_passes", "nfs_apply_Br", "nfs_cg_solve",
     "nfs_eigs", "nfs_eig_grad", "nfs_num_voxels", "nfs_device_bytes", "nfs_set_stream",
-    "nfs_destroy", "nfs_strerror",
+    "nfs_destroy", "nfs_strerror", "nfs_matvec_noalloc",
 )
+NOALLOC_MAX_VOXELS = 32768
 
 
 class NFSLibraryMissing(RuntimeError):
@@ -144,6 +145,9 @@ def lib():
     L.nfs_set_stream.restype = ip
     L.nfs_destroy.argtypes = [vp]
     L.nfs_destroy.restype = None
+    L.nfs_matvec_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ip, ip, ip,
+                                      vp, vp, dp, dp, vp, vp, vp]
+    L.nfs_matvec_noalloc.restype = ip
     L.nfs_strerror.argtypes = [ip]
     L.nfs_strerror.restype = ctypes.c_char_p
     _ = dp
@@ -311,6 +315,30 @@ class Context:
                                   ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_gam.data_ptr())),
                "nfs_eig_grad")
         return d_eps, d_gam
+
+
+def matvec_noalloc(grid, kdota, kind, axes, eps, gamma, u, out, alpha=2.0, beta=3.0, stream=None):
+    """A_r u through nfs_matvec_noalloc: no device allocation by the library.
+
+    For callers that cannot let the library allocate device memory (their
+    framework already reserved the GPU, or their budget is fixed).  eps and
+    gamma are CUDA float64 tensors in the medium layout; u and out CUDA
+    complex128 tensors of 4n elements.  Grids up to NOALLOC_MAX_VOXELS voxels,
+    unit cube, mu = 1.  Calls share one workspace inside the library, so they
+    must not overlap on the GPU."""
+    import torch
+    for t, dt in ((eps, torch.float64), (gamma, torch.float64), (u, torch.complex128), (out, torch.complex128)):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError("eps, gamma: contiguous CUDA float64; u, out: contiguous CUDA complex128")
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    k = (ctypes.c_double * 3)(*[float(x) for x in kdota])
+    kd = MEDIUM_CHIRAL if kind == "chiral" else MEDIUM_PSEUDOCHIRAL
+    st = stream if stream is not None else _current_stream()
+    code = lib().nfs_matvec_noalloc(g, k, kd, int(axes[0]), int(axes[1]), ctypes.c_void_p(eps.data_ptr()),
+                                    ctypes.c_void_p(gamma.data_ptr()), float(alpha), float(beta),
+                                    ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()), st)
+    _check(code, "nfs_matvec_noalloc")
+    return out
 
 
 def residuals(ctx: Context, omega, Y):
