@@ -6,9 +6,14 @@
 // register DFT of length N1 over elements {n1 N2 + n2}, multiplies by the
 // twiddle w_N^{n2 k1} and writes back to slot k1 N2 + n2; stage B runs, for
 // every (line, k1), a register DFT of length N2 over slots {k1 N2 + n2} and
-// writes the result to its natural position k1 + N1 k2.  Work items take the
-// line index fastest across threads: with the odd-padded pitches used by the
-// callers every shared-memory access of a warp is conflict-free.
+// writes the result to its natural position k1 + N1 k2.
+//
+// Each stage works on chunks of whole lines, one work item per thread per
+// chunk, so a thread never holds more than one item's registers.  A chunk's
+// reads and writes touch only its own lines, so the writes of chunk i and the
+// reads of chunk i + 1 share one barrier.  Work items take the line index
+// fastest across threads: with the odd-padded pitches of the callers every
+// shared-memory access of a warp is conflict-free.
 //
 // tw[m] = exp(-2 pi i m / N), m < N (forward sign; the inverse conjugates).
 // Callers must __syncthreads() before; the routine ends with a barrier.
@@ -17,20 +22,28 @@
 
 namespace nfs {
 
+template <int ITEMS_PER_LINE, int NLINES, int NT>
+struct Chunking {
+  // lines per chunk: as many whole lines as the block has threads for
+  static constexpr int LPC0 = NT / ITEMS_PER_LINE;
+  static constexpr int LPC = LPC0 < 1 ? 1 : (LPC0 > NLINES ? NLINES : LPC0);
+  static constexpr int CHUNKS = (NLINES + LPC - 1) / LPC;
+  static constexpr int ITEMS = LPC * ITEMS_PER_LINE;  // work items per chunk (<= NT when LPC0 >= 1)
+};
+
 template <bool INV, int N, int NLINES, int NT, int LS, int ES, typename C>
 __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
   using S = LineSplit<N>;
   constexpr int N1 = S::N1, N2 = S::N2;
-  constexpr int IA = NLINES * N2;
-  constexpr int PA = (IA + NT - 1) / NT;
   const int tid = threadIdx.x;
 
   if constexpr (N2 == 1) {
-    // single stage: a work item owns its whole line, so it writes in place
+    // single stage: a work item owns its whole line and writes it in place
+    constexpr int PA = (NLINES + NT - 1) / NT;
 #pragma unroll
     for (int s = 0; s < PA; ++s) {
       const int it = tid + s * NT;
-      if ((IA % NT) == 0 || it < IA) {
+      if ((NLINES % NT) == 0 || it < NLINES) {
         C* base = buf + it * LS;
         C r[N1];
 #pragma unroll
@@ -42,63 +55,66 @@ __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
     }
     __syncthreads();
   } else {
-    C ra[PA][N1];
+    // ---- stage A: items (line, n2) ----
+    {
+      using CK = Chunking<N2, NLINES, NT>;
+      C ra[N1];
+      int l = 0, n2 = 0;
+      bool act = false;
+#pragma unroll 1
+      for (int ch = 0; ch <= CK::CHUNKS; ++ch) {
+        if (ch > 0 && act) {  // write chunk ch-1
+          C* base = buf + l * LS + n2 * ES;
 #pragma unroll
-    for (int s = 0; s < PA; ++s) {
-      const int it = tid + s * NT;
-      if ((IA % NT) == 0 || it < IA) {
-        const int l = it % NLINES, n2 = it / NLINES;
-        const C* base = buf + l * LS + n2 * ES;
-#pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) ra[s][n1] = base[n1 * N2 * ES];
-        DFT<N1, INV>::run(ra[s]);
-#pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) {
-          C w = tw[n2 * k1];
-          if (INV) w.y = -w.y;
-          ra[s][k1] = cmul(ra[s][k1], w);
+          for (int k1 = 0; k1 < N1; ++k1) base[k1 * N2 * ES] = ra[k1];
         }
+        if (ch < CK::CHUNKS) {  // read chunk ch
+          l = ch * CK::LPC + tid % CK::LPC;
+          n2 = tid / CK::LPC;
+          act = tid < CK::ITEMS && l < NLINES;
+          if (act) {
+            const C* base = buf + l * LS + n2 * ES;
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) ra[n1] = base[n1 * N2 * ES];
+            DFT<N1, INV>::run(ra);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) {
+              C w = tw[n2 * k1];
+              if (INV) w.y = -w.y;
+              ra[k1] = cmul(ra[k1], w);
+            }
+          }
+        }
+        __syncthreads();
       }
     }
-    __syncthreads();
+    // ---- stage B: items (line, k1) ----
+    {
+      using CK = Chunking<N1, NLINES, NT>;
+      C rb[N2];
+      int l = 0, k1 = 0;
+      bool act = false;
+#pragma unroll 1
+      for (int ch = 0; ch <= CK::CHUNKS; ++ch) {
+        if (ch > 0 && act) {
+          C* base = buf + l * LS + k1 * ES;
 #pragma unroll
-    for (int s = 0; s < PA; ++s) {
-      const int it = tid + s * NT;
-      if ((IA % NT) == 0 || it < IA) {
-        const int l = it % NLINES, n2 = it / NLINES;
-        C* base = buf + l * LS + n2 * ES;
+          for (int k2 = 0; k2 < N2; ++k2) base[k2 * N1 * ES] = rb[k2];
+        }
+        if (ch < CK::CHUNKS) {
+          l = ch * CK::LPC + tid % CK::LPC;
+          k1 = tid / CK::LPC;
+          act = tid < CK::ITEMS && l < NLINES;
+          if (act) {
+            const C* base = buf + l * LS + k1 * N2 * ES;
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) base[k1 * N2 * ES] = ra[s][k1];
+            for (int n2 = 0; n2 < N2; ++n2) rb[n2] = base[n2 * ES];
+            DFT<N2, INV>::run(rb);
+          }
+        }
+        __syncthreads();
       }
     }
-    __syncthreads();
-
-    constexpr int IB = NLINES * N1;
-    constexpr int PB = (IB + NT - 1) / NT;
-    C rb[PB][N2];
-#pragma unroll
-    for (int s = 0; s < PB; ++s) {
-      const int it = tid + s * NT;
-      if ((IB % NT) == 0 || it < IB) {
-        const int l = it % NLINES, k1 = it / NLINES;
-        const C* base = buf + l * LS + k1 * N2 * ES;
-#pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) rb[s][n2] = base[n2 * ES];
-        DFT<N2, INV>::run(rb[s]);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < PB; ++s) {
-      const int it = tid + s * NT;
-      if ((IB % NT) == 0 || it < IB) {
-        const int l = it % NLINES, k1 = it / NLINES;
-        C* base = buf + l * LS + k1 * ES;
-#pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) base[k2 * N1 * ES] = rb[s][k2];
-      }
-    }
-    __syncthreads();
   }
 }
 

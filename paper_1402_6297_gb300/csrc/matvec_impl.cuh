@@ -16,6 +16,11 @@ __host__ __device__ constexpr int z_tile(int N3, int csize) {
   return (csize == 16 && N3 >= 96) ? 8 : 16;
 }
 __host__ __device__ constexpr int z_threads(int N3) { return N3 == 128 ? 512 : 384; }
+// Minimum resident CTAs per SM requested from the compiler (caps registers so
+// that two CTAs share an SM and overlap one's memory phase with the other's
+// shared-memory FFT).  Only where the shared memory also allows two.
+__host__ __device__ constexpr int plane_minb(int N, int csize) { return (csize == 8 && N >= 48 && N <= 96) ? 2 : 1; }
+__host__ __device__ constexpr int z_minb(int N3, int csize) { return (csize == 8 && N3 >= 48 && N3 <= 96) ? 2 : 1; }
 
 template <typename R, int NX>
 constexpr size_t plane_smem() {
@@ -37,10 +42,10 @@ template <typename R, int NX>
 static cudaError_t plane_prepare() {
   if constexpr (plane_fits<R, NX>()) {
     constexpr int NT = plane_threads(NX);
-    cudaError_t e = cudaFuncSetAttribute(k_pass1_assemble_ifft_xy<R, NX, NX, NT>,
+    cudaError_t e = cudaFuncSetAttribute(k_pass1_assemble_ifft_xy<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<R, NX>());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pass3_fft_xy_project<R, NX, NX, NT>,
+    e = cudaFuncSetAttribute(k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<R, NX>());
     return e;
   } else {
@@ -52,7 +57,7 @@ template <typename R, int N3>
 static cudaError_t z_prepare() {
   constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
   constexpr int NT = z_threads(N3);
-  return cudaFuncSetAttribute(k_pass2_z_material<R, N3, TX, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)z_smem<R, N3>());
 }
 
@@ -62,10 +67,10 @@ static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
     constexpr int NT = plane_threads(NX);
     dim3 grid(3, 2, a.n3);
     if (which == 1) {
-      k_pass1_assemble_ifft_xy<R, NX, NX, NT><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
+      k_pass1_assemble_ifft_xy<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
           a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip);
     } else {
-      k_pass3_fft_xy_project<R, NX, NX, NT><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
+      k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
           a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip);
     }
     return cudaGetLastError();
@@ -81,7 +86,7 @@ static cudaError_t z_launch(const MatvecArgs<R>& a) {
   const int ncols = a.n1 * a.n2;
   MatView<R> mv{a.inv_phi, a.gam, a.inv_mu, a.kind, a.ax_a, a.ax_b, (long long)ncols * a.n3};
   const R inv_n = (R)(1.0 / ((double)ncols * (double)a.n3));
-  k_pass2_z_material<R, N3, TX, NT><<<ncols / TX, NT, z_smem<R, N3>(), a.stream>>>(a.fld, mv, a.tw3, ncols, inv_n,
+  k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))><<<ncols / TX, NT, z_smem<R, N3>(), a.stream>>>(a.fld, mv, a.tw3, ncols, inv_n,
                                                                                  a.skip);
   return cudaGetLastError();
 }

@@ -51,6 +51,61 @@ struct MatView {
   long long n;
 };
 
+// 16-byte vector type holding 16 / sizeof(C) complex elements.
+template <typename C> struct Vec16;
+template <> struct Vec16<float2> { using type = float4; };
+template <> struct Vec16<double2> { using type = double2; };
+
+// Bursts of 16-byte global loads: thread t handles vectors t, t + NT, ...
+// (NV vectors in all), issued BATCH at a time before any is consumed, so
+// that every thread keeps BATCH requests in flight.  put(element_index, value)
+// receives each complex element.
+template <int NV, int NT, int BATCH, typename C, typename Put>
+__device__ __forceinline__ void burst_load(const C* __restrict__ src, Put put) {
+  using V = typename Vec16<C>::type;
+  constexpr int EPV = 16 / (int)sizeof(C);
+  constexpr int PER = (NV + NT - 1) / NT;
+  const V* s = reinterpret_cast<const V*>(src);
+#pragma unroll
+  for (int b0 = 0; b0 < PER; b0 += BATCH) {
+    V r[BATCH];
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int v = (b0 + b) * NT + (int)threadIdx.x;
+      if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) r[b] = __ldg(s + v);
+    }
+#pragma unroll
+    for (int b = 0; b < BATCH; ++b) {
+      const int v = (b0 + b) * NT + (int)threadIdx.x;
+      if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) {
+        if constexpr (EPV == 2) {
+          put(2 * v, mk(r[b].x, r[b].y));
+          put(2 * v + 1, mk(r[b].z, r[b].w));
+        } else {
+          put(v, r[b]);
+        }
+      }
+    }
+  }
+}
+
+// 16-byte stores: element pairs (complex64) or single elements (complex128)
+// taken from get(element_index).
+template <int NV, int NT, typename C, typename Get>
+__device__ __forceinline__ void burst_store(C* __restrict__ dst, Get get) {
+  using V = typename Vec16<C>::type;
+  constexpr int EPV = 16 / (int)sizeof(C);
+  V* d = reinterpret_cast<V*>(dst);
+  for (int v = (int)threadIdx.x; v < NV; v += NT) {
+    if constexpr (EPV == 2) {
+      const C a = get(2 * v), b = get(2 * v + 1);
+      d[v] = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+      d[v] = get(v);
+    }
+  }
+}
+
 template <typename R>
 struct Basis {
   cplx<R> c[3];
@@ -80,8 +135,16 @@ __device__ __forceinline__ void make_basis(cplx<R> a1, cplx<R> a2, cplx<R> a3, R
 // ---------------------------------------------------------------------------
 // pass 1
 // ---------------------------------------------------------------------------
-template <typename R, int NX, int NY, int NT>
-__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT)
+
+// Element range [e0, e1) of cluster rank r over a plane of NE elements, with
+// even boundaries so that 16-byte vectors never straddle two ranks.
+template <int NE>
+__device__ __forceinline__ int third_bound(int r) {
+  return r >= 3 ? NE : ((r * NE) / 3) & ~1;
+}
+
+template <typename R, int NX, int NY, int NT, int MINB>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fld,
                          const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                          const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
@@ -89,6 +152,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fl
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
+  constexpr int EPV = 16 / (int)sizeof(C);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* plane = reinterpret_cast<C*>(smem_raw);
   C* stx = plane + NY * PITCH;
@@ -102,46 +166,81 @@ k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fl
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
 
   const long long n = (long long)NE * n3;
-  const C* ua = u + (2 * grp) * n + (long long)i3 * NE;
+  const int e0 = third_bound<NE>(rank), e1 = third_bound<NE>(rank + 1);
+  const C* ua = u + (2 * grp) * n + (long long)i3 * NE + e0;
   const C* ub = ua + n;
+  // this rank's inputs, loaded with 16-byte bursts into registers (both
+  // halves in flight together)
+  using V = typename Vec16<C>::type;
+  constexpr int NVMAX = (NE / 3 + 2) / EPV;
+  constexpr int PER = (NVMAX + NT - 1) / NT;
+  const int nv = (e1 - e0) / EPV;
+  V ra[PER], rb[PER];
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int v = b * NT + (int)threadIdx.x;
+    if (v < nv) {
+      ra[b] = __ldg(reinterpret_cast<const V*>(ua) + v);
+      rb[b] = __ldg(reinterpret_cast<const V*>(ub) + v);
+    }
+  }
   const C a3 = lam[NX + NY + i3];
   C* dst0 = cl.map_shared_rank(plane, 0);
   C* dst1 = cl.map_shared_rank(plane, 1);
   C* dst2 = cl.map_shared_rank(plane, 2);
   cl.sync();  // every CTA of the cluster is resident before remote stores
 
-  const int e0 = (rank * NE) / 3, e1 = ((rank + 1) * NE) / 3;
-  for (int e = e0 + threadIdx.x; e < e1; e += NT) {
-    const int i1 = e % NX, i2 = e / NX;
-    Basis<R> B;
-    make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
-    const C va = ua[e], vb = ub[e];
-    C o[3];
-    if (grp == 0) {
-      // p^ = -c u1a + x u1b
 #pragma unroll
-      for (int k = 0; k < 3; ++k) o[k] = csub(cmul(B.x[k], vb), cmul(B.c[k], va));
-    } else {
-      // q^ = conj(x) u2a + conj(c) u2b
+  for (int b = 0; b < PER; ++b) {
+    const int v = b * NT + (int)threadIdx.x;
+    if (v < nv) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) o[k] = cadd(cmulc(B.x[k], va), cmulc(B.c[k], vb));
+      for (int h = 0; h < EPV; ++h) {
+        const int e = e0 + v * EPV + h;
+        C va, vb;
+        if constexpr (EPV == 2) {
+          va = h == 0 ? mk(ra[b].x, ra[b].y) : mk(ra[b].z, ra[b].w);
+          vb = h == 0 ? mk(rb[b].x, rb[b].y) : mk(rb[b].z, rb[b].w);
+        } else {
+          va = ra[b];
+          vb = rb[b];
+        }
+        const int i1 = e % NX, i2 = e / NX;
+        Basis<R> B;
+        make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
+        C o[3];
+        if (grp == 0) {
+          // p^ = -c u1a + x u1b
+#pragma unroll
+          for (int k = 0; k < 3; ++k) o[k] = csub(cmul(B.x[k], vb), cmul(B.c[k], va));
+        } else {
+          // q^ = conj(x) u2a + conj(c) u2b
+#pragma unroll
+          for (int k = 0; k < 3; ++k) o[k] = cadd(cmulc(B.x[k], va), cmulc(B.c[k], vb));
+        }
+        const int sidx = i2 * PITCH + i1;
+        dst0[sidx] = o[0];
+        dst1[sidx] = o[1];
+        dst2[sidx] = o[2];
+      }
     }
-    const int s = i2 * PITCH + i1;
-    dst0[s] = o[0];
-    dst1[s] = o[1];
-    dst2[s] = o[2];
   }
   cl.sync();
   smem_fft<true, NX, NY, NT, PITCH, 1>(plane, stx);  // along x (rows)
   smem_fft<true, NY, NX, NT, 1, PITCH>(plane, sty);  // along y (columns)
   C* out = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
-  for (int e = threadIdx.x; e < NE; e += NT) out[e] = plane[(e / NX) * PITCH + (e % NX)];
+  burst_store<NE / EPV, NT, C>(out, [&](int e) { return plane[(e / NX) * PITCH + (e % NX)]; });
 }
 
 // ---------------------------------------------------------------------------
 // pass 2: the material product of eq. factor_mtx, per real-space voxel:
 //   w = Phi^{-1} (xi mu^{-1} p + q),   f = mu^{-1} (zeta w + p)
 // ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ cplx<R> pick3(int k, cplx<R> a, cplx<R> b, cplx<R> c) {
+  return k == 0 ? a : (k == 1 ? b : c);
+}
+
 template <typename R>
 __device__ __forceinline__ void material_apply(const MatView<R>& m, long long v, const cplx<R>* p,
                                                const cplx<R>* q, cplx<R>* f, cplx<R>* w, R scale) {
@@ -168,32 +267,42 @@ __device__ __forceinline__ void material_apply(const MatView<R>& m, long long v,
   } else {
     const R g = m.gam[v];
     const int a = m.ax_a, b = m.ax_b;
-    C xmp[3] = {mk((R)0, (R)0), mk((R)0, (R)0), mk((R)0, (R)0)};
-    // (xi mu^{-1} p)_a = i g im_b p_b ; (.)_b = i g im_a p_a
-    xmp[a] = cmul_i(cscale(p[b], g * im[b]));
-    xmp[b] = cmul_i(cscale(p[a], g * im[a]));
+    // partner component of each axis in the coupled pair (-1: uncoupled)
     C wc[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) wc[c] = cscale(cadd(q[c], xmp[c]), ip[c]);
-    C zw[3] = {mk((R)0, (R)0), mk((R)0, (R)0), mk((R)0, (R)0)};
-    // (zeta w)_a = -i g w_b ; (.)_b = -i g w_a
-    zw[a] = cmul_mi(cscale(wc[b], g));
-    zw[b] = cmul_mi(cscale(wc[a], g));
+    for (int c = 0; c < 3; ++c) {
+      const int o = c == a ? b : (c == b ? a : -1);
+      C xmp = mk((R)0, (R)0);
+      if (o >= 0) {
+        // (xi mu^{-1} p)_c = i g im_o p_o
+        const C po = pick3<R>(o, p[0], p[1], p[2]);
+        const R imo = o == 0 ? im[0] : (o == 1 ? im[1] : im[2]);
+        xmp = cmul_i(cscale(po, g * imo));
+      }
+      wc[c] = cscale(cadd(q[c], xmp), ip[c]);
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+      const int o = c == a ? b : (c == b ? a : -1);
+      C zw = mk((R)0, (R)0);
+      if (o >= 0) zw = cmul_mi(cscale(pick3<R>(o, wc[0], wc[1], wc[2]), g));  // (zeta w)_c = -i g w_o
       w[c] = cscale(wc[c], scale);
-      f[c] = cscale(cadd(p[c], zw[c]), im[c] * scale);
+      f[c] = cscale(cadd(p[c], zw), im[c] * scale);
     }
   }
 }
 
-template <typename R, int N3, int TX, int NT>
-__global__ void __launch_bounds__(NT)
+template <typename R, int N3, int TX, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __restrict__ twz, int ncols,
                    R inv_n, const int* __restrict__ skip) {
   using C = cplx<R>;
+  using V = typename Vec16<C>::type;
+  constexpr int EPV = 16 / (int)sizeof(C);
   constexpr int LINES = 6 * TX;
   constexpr int PITCH = LINES + 1;
+  constexpr int VPR = TX / EPV;             // 16-byte vectors per (field, z) run
+  constexpr int NV = 6 * N3 * VPR;          // vectors per CTA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* stw = buf + N3 * PITCH;
@@ -201,11 +310,35 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
   for (int i = threadIdx.x; i < N3; i += NT) stw[i] = twz[i];
   const int col0 = blockIdx.x * TX;
   const long long n = (long long)ncols * N3;
-  for (int idx = threadIdx.x; idx < N3 * LINES; idx += NT) {
-    const int c = idx % TX;
-    const int t = idx / TX;
-    const int f = t % 6, z = t / 6;
-    buf[z * PITCH + f * TX + c] = fld[f * n + (long long)z * ncols + col0 + c];
+  {
+    constexpr int PER = (NV + NT - 1) / NT;
+    constexpr int BATCH = PER < 8 ? PER : 8;
+#pragma unroll
+    for (int b0 = 0; b0 < PER; b0 += BATCH) {
+      V r[BATCH];
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b) {
+        const int v = (b0 + b) * NT + (int)threadIdx.x;
+        if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) {
+          const int cv = v % VPR, t = v / VPR, f = t % 6, z = t / 6;
+          r[b] = *(reinterpret_cast<const V*>(fld + f * n + (long long)z * ncols + col0) + cv);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < BATCH; ++b) {
+        const int v = (b0 + b) * NT + (int)threadIdx.x;
+        if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) {
+          const int cv = v % VPR, t = v / VPR, f = t % 6, z = t / 6;
+          C* d = buf + z * PITCH + f * TX + cv * EPV;
+          if constexpr (EPV == 2) {
+            d[0] = mk(r[b].x, r[b].y);
+            d[1] = mk(r[b].z, r[b].w);
+          } else {
+            d[0] = r[b];
+          }
+        }
+      }
+    }
   }
   __syncthreads();
   smem_fft<true, N3, LINES, NT, 1, PITCH>(buf, stw);
@@ -225,19 +358,23 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
   }
   __syncthreads();
   smem_fft<false, N3, LINES, NT, 1, PITCH>(buf, stw);
-  for (int idx = threadIdx.x; idx < N3 * LINES; idx += NT) {
-    const int c = idx % TX;
-    const int t = idx / TX;
-    const int f = t % 6, z = t / 6;
-    fld[f * n + (long long)z * ncols + col0 + c] = buf[z * PITCH + f * TX + c];
+  for (int v = threadIdx.x; v < NV; v += NT) {
+    const int cv = v % VPR, t = v / VPR, f = t % 6, z = t / 6;
+    const C* s = buf + z * PITCH + f * TX + cv * EPV;
+    V* d = reinterpret_cast<V*>(fld + f * n + (long long)z * ncols + col0) + cv;
+    if constexpr (EPV == 2) {
+      *d = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+    } else {
+      *d = s[0];
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // pass 3
 // ---------------------------------------------------------------------------
-template <typename R, int NX, int NY, int NT>
-__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT)
+template <typename R, int NX, int NY, int NT, int MINB>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au,
                        const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                        const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
@@ -245,6 +382,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
+  constexpr int EPV = 16 / (int)sizeof(C);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* plane = reinterpret_cast<C*>(smem_raw);
   C* stx = plane + NY * PITCH;
@@ -257,7 +395,9 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
   const C* in = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
-  for (int e = threadIdx.x; e < NE; e += NT) plane[(e / NX) * PITCH + (e % NX)] = in[e];
+  constexpr int PER = (NE / EPV + NT - 1) / NT;
+  burst_load<NE / EPV, NT, (PER < 12 ? PER : 12), C>(
+      in, [&](int e, C v) { plane[(e / NX) * PITCH + (e % NX)] = v; });
   __syncthreads();
   smem_fft<false, NX, NY, NT, PITCH, 1>(plane, stx);
   smem_fft<false, NY, NX, NT, 1, PITCH>(plane, sty);
@@ -269,25 +409,37 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   C* o0 = Au + (2 * grp) * n + (long long)i3 * NE;
   C* o1 = o0 + n;
   const C a3 = lam[NX + NY + i3];
-  const int e0 = (rank * NE) / 3, e1 = ((rank + 1) * NE) / 3;
-  for (int e = e0 + threadIdx.x; e < e1; e += NT) {
-    const int i1 = e % NX, i2 = e / NX;
-    const int s = i2 * PITCH + i1;
-    const C f[3] = {src0[s], src1[s], src2[s]};
-    Basis<R> B;
-    make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
-    C r0, r1;
-    if (grp == 0) {
-      // P_r^* f = [-sum conj(c) f ; sum conj(x) f]
-      r0 = cneg(cadd(cadd(cmulc(B.c[0], f[0]), cmulc(B.c[1], f[1])), cmulc(B.c[2], f[2])));
-      r1 = cadd(cadd(cmulc(B.x[0], f[0]), cmulc(B.x[1], f[1])), cmulc(B.x[2], f[2]));
-    } else {
-      // Q_r^* w = [sum x w ; sum c w]
-      r0 = cadd(cadd(cmul(B.x[0], f[0]), cmul(B.x[1], f[1])), cmul(B.x[2], f[2]));
-      r1 = cadd(cadd(cmul(B.c[0], f[0]), cmul(B.c[1], f[1])), cmul(B.c[2], f[2]));
+  const int e0 = third_bound<NE>(rank), e1 = third_bound<NE>(rank + 1);
+  // element pairs (i1 even) so that the two outputs leave as 16-byte stores
+  for (int ep = e0 / 2 + threadIdx.x; ep < e1 / 2; ep += NT) {
+    C r0[2], r1[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = 2 * ep + h;
+      const int i1 = e % NX, i2 = e / NX;
+      const int s = i2 * PITCH + i1;
+      const C f[3] = {src0[s], src1[s], src2[s]};
+      Basis<R> B;
+      make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
+      if (grp == 0) {
+        // P_r^* f = [-sum conj(c) f ; sum conj(x) f]
+        r0[h] = cneg(cadd(cadd(cmulc(B.c[0], f[0]), cmulc(B.c[1], f[1])), cmulc(B.c[2], f[2])));
+        r1[h] = cadd(cadd(cmulc(B.x[0], f[0]), cmulc(B.x[1], f[1])), cmulc(B.x[2], f[2]));
+      } else {
+        // Q_r^* w = [sum x w ; sum c w]
+        r0[h] = cadd(cadd(cmul(B.x[0], f[0]), cmul(B.x[1], f[1])), cmul(B.x[2], f[2]));
+        r1[h] = cadd(cadd(cmul(B.c[0], f[0]), cmul(B.c[1], f[1])), cmul(B.c[2], f[2]));
+      }
     }
-    o0[e] = r0;
-    o1[e] = r1;
+    if constexpr (EPV == 2) {
+      reinterpret_cast<float4*>(o0)[ep] = make_float4(r0[0].x, r0[0].y, r0[1].x, r0[1].y);
+      reinterpret_cast<float4*>(o1)[ep] = make_float4(r1[0].x, r1[0].y, r1[1].x, r1[1].y);
+    } else {
+      o0[2 * ep] = r0[0];
+      o0[2 * ep + 1] = r0[1];
+      o1[2 * ep] = r1[0];
+      o1[2 * ep + 1] = r1[1];
+    }
   }
   cl.sync();  // keep this CTA's plane alive until the cluster finished reading it
 }
