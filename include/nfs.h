@@ -206,6 +206,37 @@ int nfs_matvec_noalloc(const int grid[3], const double k[3], int kind, int axis_
                        const double* eps, const double* gamma, double alpha, double beta,
                        const void* u, void* Au, void* stream);
 
+/* ---- batches of independent problems ------------------------------------ */
+
+/* A band structure (Section 5.3 sweeps k along G-X-M-R-G) is a set of
+ * independent eigenproblems.  A batch solves many of them at once: problems
+ * that share a grid (and medium kind, pseudochiral axis pair and mu-ness) form
+ * one class whose P problems run through every kernel in single launches, in
+ * lock-step, with the CG iterations replayed from a captured CUDA graph; the
+ * classes run concurrently, one host thread and stream each. */
+typedef struct nfs_batch nfs_batch;
+
+typedef struct {
+  int grid[3];           /* as for nfs_setup; unit cube lattice (a = 1)            */
+  double k[3];           /* Bloch vector / 2 pi                                      */
+  nfs_material mat;      /* host pointers, copied by nfs_setup_batch                 */
+} nfs_problem;
+
+/* Validate and set up nprob problems (the checks of nfs_setup apply to each).
+ * opt as for nfs_setup (shared by all problems; its stream orders the batch
+ * after earlier work).  On error *out is NULL. */
+int nfs_setup_batch(nfs_batch** out, int nprob, const nfs_problem* probs, const nfs_options* opt);
+
+/* The nev smallest positive eigenvalues of every problem, as nfs_eigs.
+ * omega: HOST [nprob][nev]; info: HOST [nprob] or NULL.  Returns the worst
+ * status (NFS_ENOCONV if any problem hit the restart cap). */
+int nfs_eigs_batch(nfs_batch* b, int nev, double* omega, nfs_eigs_info* info);
+
+/* Number of grid classes the batch was split into. */
+int nfs_batch_num_classes(const nfs_batch* b);
+
+void nfs_destroy_batch(nfs_batch* b);
+
 /* Basic facts about a context: n, and device bytes held. */
 long long nfs_num_voxels(const nfs_ctx* ctx);
 long long nfs_device_bytes(const nfs_ctx* ctx);

@@ -1,0 +1,64 @@
+"""torch.autograd wrapper: eigenvalues as a differentiable function of the
+per-voxel permittivity and chirality.
+
+Forward runs nfs_setup + nfs_eigs; backward calls nfs_eig_grad with the
+incoming gradient as the weights, i.e. the adjoint d(sum_j g_j omega_j) /
+d(eps, gamma) = sum_j g_j y_j^* (dA_r) y_j / (y_j^* B_r y_j) evaluated by the
+hand-written CUDA kernel.  Both steps run in libnfs; this module only moves
+tensors.  The gradient of a single eigenvalue inside a degenerate cluster is
+not defined; the gradient of a sum over a complete cluster is.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import workloads as wl
+
+from . import nfs
+
+
+def _as_components(t, shape3):
+    a = t.detach().to("cpu", torch.float64).numpy()
+    if a.shape == shape3[1:]:
+        return np.broadcast_to(a, shape3).copy(), True
+    if a.shape == shape3:
+        return np.ascontiguousarray(a), False
+    raise ValueError(f"expected a per-voxel {shape3[1:]} or per-component {shape3} array, got {a.shape}")
+
+
+class NSFEigenvalues(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, eps, gamma, grid, kdota, nev, precision, options):
+        n1, n2, n3 = grid
+        shape3 = (3, n3, n2, n1)
+        e, eps_voxel = _as_components(eps, shape3)
+        g, gam_voxel = _as_components(gamma, shape3)
+        medium = wl.Medium(tuple(grid), "chiral", e, g)
+        ctx = nfs.Context(grid, kdota, medium, precision=precision, **options)
+        omega, Y, _ = ctx.eigs(nev, vectors=True)
+        fctx.nfs_ctx = ctx
+        fctx.Y = Y
+        fctx.flags = (eps_voxel, gam_voxel, eps.dtype, eps.device, gamma.dtype, gamma.device)
+        return torch.as_tensor(omega, dtype=torch.float64, device=eps.device)
+
+    @staticmethod
+    def backward(fctx, grad_omega):
+        eps_voxel, gam_voxel, edt, edev, gdt, gdev = fctx.flags
+        w = grad_omega.detach().to("cpu", torch.float64).numpy()
+        d_eps, d_gam = fctx.nfs_ctx.eig_grad(fctx.Y, w)
+        if eps_voxel:
+            d_eps = d_eps.sum(0)
+        if gam_voxel:
+            d_gam = d_gam.sum(0)
+        fctx.nfs_ctx.close()
+        return d_eps.to(edev, edt), d_gam.to(gdev, gdt), None, None, None, None, None
+
+
+def chiral_eigenvalues(eps, gamma, grid, kdota, nev=5, precision="fp64", **options):
+    """The nev smallest positive eigenvalues of a chiral medium (mu = 1) given
+    eps and gamma either per voxel (n3, n2, n1) -- the same value for the three
+    field components -- or per component (3, n3, n2, n1); differentiable with
+    respect to both."""
+    return NSFEigenvalues.apply(eps, gamma, tuple(grid), tuple(kdota), int(nev), precision, dict(options))

@@ -1,9 +1,13 @@
 // Vector kernels of the CG and Lanczos loops (Section 4.2: CG on A_r u = b;
-// invert Lanczos on (B_r, A_r)).  Reductions are deterministic: a fixed grid
-// of kRedBlocks blocks writes one partial per block, and a one-block kernel
-// sums the partials in a fixed order.  Every CG kernel reads the device
-// `done` flag first and returns at once when it is set, so a batch of
-// launched iterations past convergence costs only empty launches.
+// invert Lanczos on (B_r, A_r)), batched over the P problems of one context:
+// problem p's vectors sit at base + p * N (N = 4n), and the problem index comes
+// from a grid dimension, so a launch serves every problem at once.
+//
+// Reductions are deterministic: a fixed grid of kRedBlocks blocks per problem
+// writes one partial per block, and a one-block kernel sums the partials in a
+// fixed order.  Every CG kernel reads its problem's device `done` flag first
+// and returns at once when it is set, so launched iterations past convergence
+// (or for problems already converged) cost only empty launches.
 #pragma once
 #include <cstdint>
 
@@ -13,8 +17,9 @@ namespace nfs {
 
 constexpr int kRedBlocks = 304;   // two blocks per SM on a 152-SM GB300
 constexpr int kRedThreads = 256;
+constexpr int kMaxPartials = 1024;  // >= 6 * n3 (pass-3 CTAs) and kRedBlocks
 
-// CG scalar state, device resident.
+// CG scalar state of one problem, device resident (an array of P).
 struct CGState {
   double rr;        // r^* r of the current residual
   double pAp;       // p^* A p
@@ -23,8 +28,38 @@ struct CGState {
   int it, maxit;
   int done;         // 1: converged, broken down or out of iterations
   int status;       // 0, -6 (no convergence) or -7 (breakdown)
-  double part_a[kRedBlocks];
-  double part_b[kRedBlocks];
+  int npart_a;      // number of valid entries of part_a
+  int pad_;
+  double part_a[kMaxPartials];  // partials of p^* A p (written by pass 3 or k_dot_re)
+  double part_b[kMaxPartials];  // partials of r^* r
+};
+constexpr long long kStateDoubles = sizeof(CGState) / sizeof(double);
+constexpr int kStateInts = (int)(sizeof(CGState) / sizeof(int));
+static_assert(sizeof(CGState) % sizeof(double) == 0, "CGState must be a whole number of doubles");
+
+// Partial sums of complex products: single-precision data accumulate in FP32
+// over short runs that are folded into FP64 (FP64 arithmetic is scarce on
+// this GPU); double-precision data accumulate in FP64.
+template <typename C>
+struct Acc {
+  double d = 0.0;
+  __device__ __forceinline__ void add(double v) { d += v; }
+  __device__ __forceinline__ double total() const { return d; }
+};
+template <>
+struct Acc<float2> {
+  double d = 0.0;
+  float f = 0.f;
+  int k = 0;
+  __device__ __forceinline__ void add(float v) {
+    f += v;
+    if (++k == 16) {
+      d += (double)f;
+      f = 0.f;
+      k = 0;
+    }
+  }
+  __device__ __forceinline__ double total() const { return d + (double)f; }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -33,7 +68,7 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum over the block; the result is valid in thread 0.
+// Sum over the block; the result is valid in thread 0 (and warp 0) only.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sh[NT / 32];
@@ -50,66 +85,85 @@ __device__ __forceinline__ double block_sum(double v) {
   return r;
 }
 
-__device__ __forceinline__ double sum_partials(const double* part) {
-  // one block of kRedThreads threads sums kRedBlocks partials in fixed order
+__device__ __forceinline__ double sum_partials(const double* part, int count = kRedBlocks) {
+  // one block of kRedThreads threads sums `count` partials in fixed order
   double v = 0.0;
-  for (int i = threadIdx.x; i < kRedBlocks; i += kRedThreads) v += part[i];
+  for (int i = threadIdx.x; i < count; i += kRedThreads) v += part[i];
   return block_sum<kRedThreads>(v);
 }
 
-// part[b] = sum over block b of Re(conj(x) y)
+// part[p * pstride + b] = block b's share of Re(conj(x_p) y_p); grid (kRedBlocks, P).
+// skip (optional): problem p is skipped when skip[p * sstride] is nonzero.
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads)
-k_dot_re(const C* __restrict__ x, const C* __restrict__ y, long long N, double* __restrict__ part,
-         const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  double acc = 0.0;
+k_dot_re(const C* __restrict__ x, const C* __restrict__ y, long long N, double* __restrict__ part, long long pstride,
+         const int* __restrict__ skip, int sstride) {
+  const int p = blockIdx.y;
+  if (skip && skip[(long long)p * sstride]) return;
+  x += (long long)p * N;
+  y += (long long)p * N;
+  Acc<C> acc;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
     const C a = x[i], b = y[i];
-    acc += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+    acc.add(a.x * b.x + a.y * b.y);
   }
-  const double s = block_sum<kRedThreads>(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+  const double s = block_sum<kRedThreads>(acc.total());
+  if (threadIdx.x == 0) part[(long long)p * pstride + blockIdx.x] = s;
 }
 
-// CG start: rr = sum part_a; stop once r^* r <= tol2 (absolute threshold).
-__global__ void __launch_bounds__(kRedThreads) k_cg_init(CGState* st, double tol2, int maxit) {
+// CG start, one block per problem: rr = sum part_a; stop once r^* r <= tol2[p].
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_init(CGState* st, const double* __restrict__ tol2, int maxit, int npart_a) {
+  st += blockIdx.x;
   const double rr = sum_partials(st->part_a);
   if (threadIdx.x == 0) {
+    const double t2 = tol2[blockIdx.x];
+    st->npart_a = npart_a;
     st->rr = rr;
-    st->tol2 = tol2;
+    st->tol2 = t2;
     st->it = 0;
     st->maxit = maxit;
     st->status = 0;
     st->alpha = st->beta = 0.0;
-    st->done = (rr <= tol2) ? 1 : 0;
+    st->done = (rr <= t2) ? 1 : 0;
     if (!(rr == rr)) { st->done = 1; st->status = -7; }
   }
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_cg_alpha(CGState* st) {
-  if (st->done) return;
-  const double pAp = sum_partials(st->part_a);
-  if (threadIdx.x == 0) {
-    st->pAp = pAp;
-    if (!(pAp > 0.0)) {  // also catches NaN
-      st->status = -7;
-      st->done = 1;
-    } else {
-      st->alpha = st->rr / pAp;
-    }
-  }
-}
-
-// x += alpha p ; r -= alpha Ap ; part_b[block] = partial r^* r
+// alpha = rr / p^*Ap (every block sums the npart_a partials in the same
+// order, so all blocks agree; block 0 records it), then
+// x += alpha p ; r -= alpha Ap ; part_b[block] = partial r^* r.  Grid (kRedBlocks, P).
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __restrict__ p, const C* __restrict__ Ap, long long N,
                CGState* st) {
+  const int pb = blockIdx.y;
+  st += pb;
   if (st->done) return;
+  x += (long long)pb * N;
+  r += (long long)pb * N;
+  p += (long long)pb * N;
+  Ap += (long long)pb * N;
   using R = typename RealOf<C>::type;
-  const R al = (R)st->alpha;
-  double acc = 0.0;
+  __shared__ double s_alpha;
+  __shared__ int s_ok;
+  const double pAp = sum_partials(st->part_a, st->npart_a);  // valid in thread 0 only
+  if (threadIdx.x == 0) {
+    s_alpha = st->rr / pAp;
+    s_ok = (pAp > 0.0) && (s_alpha == s_alpha);  // also catches NaN
+    if (blockIdx.x == 0) {
+      st->pAp = pAp;
+      st->alpha = s_alpha;
+      if (!s_ok) {
+        st->status = -7;
+        st->done = 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (!s_ok) return;  // breakdown: leave x, r untouched (uniform per block)
+  const R al = (R)s_alpha;
+  Acc<C> acc;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
     const C pi = p[i], api = Ap[i];
     C xi = x[i], ri = r[i];
@@ -119,13 +173,15 @@ k_cg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __restrict__ p, co
     ri.y -= al * api.y;
     x[i] = xi;
     r[i] = ri;
-    acc += (double)ri.x * (double)ri.x + (double)ri.y * (double)ri.y;
+    acc.add(ri.x * ri.x + ri.y * ri.y);
   }
-  const double s = block_sum<kRedThreads>(acc);
+  const double s = block_sum<kRedThreads>(acc.total());
   if (threadIdx.x == 0) st->part_b[blockIdx.x] = s;
 }
 
+// One block per problem: new residual norm, convergence, beta.
 __global__ void __launch_bounds__(kRedThreads) k_cg_beta(CGState* st) {
+  st += blockIdx.x;
   if (st->done) return;
   const double rr = sum_partials(st->part_b);
   if (threadIdx.x == 0) {
@@ -144,80 +200,74 @@ __global__ void __launch_bounds__(kRedThreads) k_cg_beta(CGState* st) {
   }
 }
 
-// p = r + beta p
-template <typename C>
-__global__ void __launch_bounds__(kRedThreads)
-k_cg_update_p(C* __restrict__ p, const C* __restrict__ r, long long N, CGState* st) {
-  if (st->done) return;
-  using R = typename RealOf<C>::type;
-  const R be = (R)st->beta;
-  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
-    const C ri = r[i];
-    C pi = p[i];
-    pi.x = ri.x + be * pi.x;
-    pi.y = ri.y + be * pi.y;
-    p[i] = pi;
-  }
-}
-
 // ---------------------------------------------------------------------------
-// Elementwise helpers
+// Elementwise helpers over all P problems (flat index i, problem i / N)
 // ---------------------------------------------------------------------------
 
-// y = a - b
 template <typename C>
-__global__ void k_sub(const C* __restrict__ a, const C* __restrict__ b, C* __restrict__ y, long long N) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+__global__ void k_sub(const C* __restrict__ a, const C* __restrict__ b, C* __restrict__ y, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
     y[i] = csub(a[i], b[i]);
 }
 
-// complex64 <- complex128 * s
-__global__ void k_demote(const double2* __restrict__ a, double s, float2* __restrict__ y, long long N) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+// complex64 <- complex128 * s[problem]
+__global__ void k_demote(const double2* __restrict__ a, const double* __restrict__ s, float2* __restrict__ y,
+                         long long N, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const double2 v = a[i];
-    y[i] = make_float2((float)(v.x * s), (float)(v.y * s));
+    const double f = s[i / N];
+    y[i] = make_float2((float)(v.x * f), (float)(v.y * f));
   }
 }
 
-// x += s * complex128(d)
-__global__ void k_axpy_promote(double2* __restrict__ x, double s, const float2* __restrict__ d, long long N) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+// x += s[problem] * complex128(d)
+__global__ void k_axpy_promote(double2* __restrict__ x, const double* __restrict__ s, const float2* __restrict__ d,
+                               long long N, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const float2 v = d[i];
+    const double f = s[i / N];
     double2 xi = x[i];
-    xi.x += s * (double)v.x;
-    xi.y += s * (double)v.y;
+    xi.x += f * (double)v.x;
+    xi.y += f * (double)v.y;
     x[i] = xi;
   }
 }
 
+// a *= s[problem]
 template <typename C>
-__global__ void k_scale(C* __restrict__ a, double s, long long N) {
+__global__ void k_scale(C* __restrict__ a, const double* __restrict__ s, long long N, long long total) {
   using R = typename RealOf<C>::type;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    a[i] = cscale(a[i], (R)s);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    a[i] = cscale(a[i], (R)s[i / N]);
 }
 
 // B_r v = i [Sigma^{-1} v2 ; -Sigma^{-1} v1], Sigma_r = diag(sqrt(Lq), sqrt(Lq))
-// (eq. NFSEP_spd_1).  lam holds Lambda_1 | Lambda_2 | Lambda_3.
+// (eq. NFSEP_spd_1).  lam holds Lambda_1 | Lambda_2 | Lambda_3 per problem
+// (stride n1 + n2 + n3); v and out hold P vectors of 4n.
 __global__ void k_apply_Br(const double2* __restrict__ v, double2* __restrict__ out, const double2* __restrict__ lam,
-                           int n1, int n2, int n3) {
+                           int n1, int n2, int n3, int P) {
   const long long n = (long long)n1 * n2 * n3;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+  const int nl = n1 + n2 + n3;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n * P; g += (long long)gridDim.x * blockDim.x) {
+    const long long p = g / n, e = g % n;
     const int i1 = (int)(e % n1);
     const int i2 = (int)((e / n1) % n2);
     const int i3 = (int)(e / ((long long)n1 * n2));
-    const double lq = cabs2(lam[i1]) + cabs2(lam[n1 + i2]) + cabs2(lam[n1 + n2 + i3]);
+    const double2* L = lam + p * nl;
+    const double lq = cabs2(L[i1]) + cabs2(L[n1 + i2]) + cabs2(L[n1 + n2 + i3]);
     const double is = 1.0 / sqrt(lq);
-    const double2 v1a = v[e], v1b = v[n + e], v2a = v[2 * n + e], v2b = v[3 * n + e];
-    out[e] = cmul_i(cscale(v2a, is));
-    out[n + e] = cmul_i(cscale(v2b, is));
-    out[2 * n + e] = cmul_mi(cscale(v1a, is));
-    out[3 * n + e] = cmul_mi(cscale(v1b, is));
+    const double2* vp = v + p * 4 * n;
+    double2* op = out + p * 4 * n;
+    const double2 v1a = vp[e], v1b = vp[n + e], v2a = vp[2 * n + e], v2b = vp[3 * n + e];
+    op[e] = cmul_i(cscale(v2a, is));
+    op[n + e] = cmul_i(cscale(v2b, is));
+    op[2 * n + e] = cmul_mi(cscale(v1a, is));
+    op[3 * n + e] = cmul_mi(cscale(v1b, is));
   }
 }
 
 // Counter-based uniform numbers in [-1, 1) (splitmix64 finaliser of the
-// element index and seed): the Lanczos starting vector.
+// element index and seed): the Lanczos starting vectors.
 __device__ __forceinline__ double u01_hash(unsigned long long x) {
   x += 0x9E3779B97F4A7C15ull;
   x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -226,22 +276,32 @@ __device__ __forceinline__ double u01_hash(unsigned long long x) {
   return (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
 }
 
-__global__ void k_random_fill(double2* __restrict__ v, long long N, unsigned long long seed) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+// Problem p's starting vector at v + p * vstride (N entries).
+__global__ void k_random_fill(double2* __restrict__ v, long long N, long long vstride, int P, unsigned long long seed) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N * P; g += (long long)gridDim.x * blockDim.x) {
+    const long long p = g / N, i = g % N;
     const unsigned long long k = (unsigned long long)i * 2ull + seed * 0x632BE59BD9B4E019ull;
-    v[i] = make_double2(u01_hash(k), u01_hash(k + 1));
+    v[p * vstride + i] = make_double2(u01_hash(k), u01_hash(k + 1));
   }
 }
 
 // ---------------------------------------------------------------------------
-// Lanczos: basis stored contiguously, vector j at V + j * N (complex128).
+// Lanczos.  Problem p's basis: vector j at V + p * vstride + j * N (complex128),
+// its new vector w at w + p * N.  Coefficients per problem at c + p * m * 2.
 // ---------------------------------------------------------------------------
 
-// part[(b * m + j) * 2 + {0,1}] = block b's share of conj(V_j)^T w, j < m
+// part[((p * gridDim.x + b) * m + j) * 2 + {0,1}] = block b's share of
+// conj(V_pj)^T w_p, j < m; grid (kRedBlocks, P).
 template <int NT>
 __global__ void __launch_bounds__(NT)
-k_multi_dot(const double2* __restrict__ V, int m, const double2* __restrict__ w, long long N, double* __restrict__ part) {
-  constexpr int EPT = 4;  // elements of w kept in registers per thread and pass
+k_multi_dot(const double2* __restrict__ V, long long vstride, int m, const double2* __restrict__ w, long long N,
+            double* __restrict__ part, const int* __restrict__ active) {
+  constexpr int EPT = 4;  // elements of w per thread and pass
+  const int p = blockIdx.y;
+  if (active && !active[p]) return;
+  V += (long long)p * vstride;
+  w += (long long)p * N;
+  double* pp = part + ((long long)p * gridDim.x + blockIdx.x) * m * 2;
   for (int j0 = 0; j0 < m; ++j0) {
     double re = 0.0, im = 0.0;
     for (long long base = (long long)blockIdx.x * NT * EPT; base < N; base += (long long)gridDim.x * NT * EPT) {
@@ -258,32 +318,42 @@ k_multi_dot(const double2* __restrict__ V, int m, const double2* __restrict__ w,
     re = block_sum<NT>(re);
     im = block_sum<NT>(im);
     if (threadIdx.x == 0) {
-      part[((long long)blockIdx.x * m + j0) * 2 + 0] = re;
-      part[((long long)blockIdx.x * m + j0) * 2 + 1] = im;
+      pp[j0 * 2 + 0] = re;
+      pp[j0 * 2 + 1] = im;
     }
   }
 }
 
-// out[j] = sum over nb blocks of part[b][j]  (one block per j)
+// out[(p * m + j) * 2 + {0,1}] = sum over nb blocks; grid (m, P)
 __global__ void __launch_bounds__(kRedThreads)
-k_multi_dot_finish(const double* __restrict__ part, int m, int nb, double* __restrict__ out) {
-  const int j = blockIdx.x;
+k_multi_dot_finish(const double* __restrict__ part, int m, int nb, double* __restrict__ out,
+                   const int* __restrict__ active) {
+  const int j = blockIdx.x, p = blockIdx.y;
+  if (active && !active[p]) return;
   double re = 0.0, im = 0.0;
   for (int b = threadIdx.x; b < nb; b += kRedThreads) {
-    re += part[((long long)b * m + j) * 2 + 0];
-    im += part[((long long)b * m + j) * 2 + 1];
+    re += part[(((long long)p * nb + b) * m + j) * 2 + 0];
+    im += part[(((long long)p * nb + b) * m + j) * 2 + 1];
   }
   re = block_sum<kRedThreads>(re);
   im = block_sum<kRedThreads>(im);
   if (threadIdx.x == 0) {
-    out[2 * j] = re;
-    out[2 * j + 1] = im;
+    out[((long long)p * m + j) * 2] = re;
+    out[((long long)p * m + j) * 2 + 1] = im;
   }
 }
 
-// w -= sum_j c_j V_j ; Mw -= sum_j c_j MV_j  (c complex, m entries)
+// w_p -= sum_j c_pj V_pj ; Mw_p -= sum_j c_pj MV_pj; grid (blocks, P).
 __global__ void k_multi_axpy(double2* __restrict__ w, double2* __restrict__ Mw, const double2* __restrict__ V,
-                             const double2* __restrict__ MV, const double* __restrict__ c, int m, long long N) {
+                             const double2* __restrict__ MV, long long vstride, const double* __restrict__ c, int m,
+                             long long N, const int* __restrict__ active) {
+  const int p = blockIdx.y;
+  if (active && !active[p]) return;
+  w += (long long)p * N;
+  Mw += (long long)p * N;
+  V += (long long)p * vstride;
+  MV += (long long)p * vstride;
+  c += (long long)p * m * 2;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     double2 a = w[i], b = Mw[i];
     for (int j = 0; j < m; ++j) {
@@ -297,10 +367,16 @@ __global__ void k_multi_axpy(double2* __restrict__ w, double2* __restrict__ Mw, 
   }
 }
 
-// In-place basis rotation V[:, 0:k] = V[:, 0:m] Y (Y real, m x k, column-major).
-// Each block stages TE elements of all m vectors in shared memory first.
+// In-place basis rotation V_p[:, 0:k] = V_p[:, 0:m] Y_p (Y_p real, m x k,
+// column-major, at Y + p * m * k); grid (blocks, P).  Each block stages TE
+// elements of all m vectors in shared memory first.
 template <int TE>
-__global__ void k_rotate_basis(double2* __restrict__ V, int m, const double* __restrict__ Y, int k, long long N) {
+__global__ void k_rotate_basis(double2* __restrict__ V, long long vstride, int m, const double* __restrict__ Y, int k,
+                               long long N, const int* __restrict__ active) {
+  const int p = blockIdx.y;
+  if (active && !active[p]) return;
+  V += (long long)p * vstride;
+  Y += (long long)p * m * k;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tile = reinterpret_cast<double2*>(smem_raw);  // [m][TE]
   for (long long base = (long long)blockIdx.x * TE; base < N; base += (long long)gridDim.x * TE) {
@@ -323,6 +399,114 @@ __global__ void k_rotate_basis(double2* __restrict__ V, int m, const double* __r
       if (i < N) V[(long long)col * N + i] = acc;
     }
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Orthogonality monitor: inner products of a new Lanczos vector with complex64
+// shadow copies of A_r V.  They measure the basis's loss of orthogonality to
+// about 1e-7 / sqrt(N) (single-precision products, FP64 block sums), which is
+// enough to decide when an exact FP64 re-orthogonalisation is due; they never
+// enter the basis or the projected matrix.  Shadows are laid out like the FP64
+// basis (vstride per problem, N per vector).
+// ---------------------------------------------------------------------------
+
+// y[p * ystride + i] = complex64(a[p * astride + i]), i < len, p < P
+__global__ void k_to_c64(const double2* __restrict__ a, long long astride, float2* __restrict__ y, long long ystride,
+                         long long len, int P) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < len * P; g += (long long)gridDim.x * blockDim.x) {
+    const long long p = g / len, i = g % len;
+    const double2 v = a[p * astride + i];
+    y[p * ystride + i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// part[(((p * m + j) * gridDim.x) + b) * 2 + {0, 1}] = block b's share of
+// conj(S_pj)^T w32_p for the G vectors j = blockIdx.y * G + g < m; grid
+// (kRedBlocks, ceil(m / G), P).
+template <int G>
+__global__ void __launch_bounds__(kRedThreads)
+k_shadow_dots(const float2* __restrict__ S, long long sstride, int m, const float2* __restrict__ w32, long long N,
+              double* __restrict__ part, const int* __restrict__ active) {
+  const int p = blockIdx.z;
+  if (active && !active[p]) return;
+  S += (long long)p * sstride;
+  w32 += (long long)p * N;
+  const int j0 = blockIdx.y * G;
+  float re[G], im[G];
+  double dre[G], dim[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    re[g] = im[g] = 0.f;
+    dre[g] = dim[g] = 0.0;
+  }
+  int cnt = 0;
+  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
+    const float2 b = w32[i];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (j0 + g < m) {
+        const float2 a = S[(long long)(j0 + g) * N + i];
+        re[g] += a.x * b.x + a.y * b.y;
+        im[g] += a.x * b.y - a.y * b.x;
+      }
+    }
+    if (++cnt == 16) {  // fold short single-precision runs into FP64
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        dre[g] += re[g];
+        dim[g] += im[g];
+        re[g] = im[g] = 0.f;
+      }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const double sr = block_sum<kRedThreads>(dre[g] + re[g]);
+    const double si = block_sum<kRedThreads>(dim[g] + im[g]);
+    if (threadIdx.x == 0 && j0 + g < m) {
+      const long long o = (((long long)p * m + j0 + g) * gridDim.x + blockIdx.x) * 2;
+      part[o] = sr;
+      part[o + 1] = si;
+    }
+  }
+}
+
+// out[(p * m + j) * 2 + {0,1}] = sum over nb blocks; grid (m, P)
+__global__ void __launch_bounds__(kRedThreads)
+k_dots_finish(const double* __restrict__ part, int m, int nb, double* __restrict__ out, const int* __restrict__ active) {
+  const int j = blockIdx.x, p = blockIdx.y;
+  if (active && !active[p]) return;
+  double re = 0.0, im = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kRedThreads) {
+    re += part[(((long long)p * m + j) * nb + b) * 2 + 0];
+    im += part[(((long long)p * m + j) * nb + b) * 2 + 1];
+  }
+  re = block_sum<kRedThreads>(re);
+  im = block_sum<kRedThreads>(im);
+  if (threadIdx.x == 0) {
+    out[((long long)p * m + j) * 2] = re;
+    out[((long long)p * m + j) * 2 + 1] = im;
+  }
+}
+
+// New basis vector j of every active problem: V_pj = s_p w_p, MV_pj = s_p Mw_p
+// in FP64, plus their complex64 shadows.
+__global__ void k_store_basis_vector(const double2* __restrict__ w, const double2* __restrict__ Mw,
+                                     const double* __restrict__ s, double2* __restrict__ V, double2* __restrict__ MV,
+                                     float2* __restrict__ V32, float2* __restrict__ MV32, long long vstride, int j,
+                                     long long N, int P, const int* __restrict__ active) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N * P; g += (long long)gridDim.x * blockDim.x) {
+    const long long p = g / N, i = g % N;
+    if (active && !active[p]) continue;
+    const double f = s[p];
+    const double2 a = cscale(w[g], f), b = cscale(Mw[g], f);
+    const long long o = p * vstride + (long long)j * N + i;
+    V[o] = a;
+    MV[o] = b;
+    V32[o] = make_float2((float)a.x, (float)a.y);
+    MV32[o] = make_float2((float)b.x, (float)b.y);
   }
 }
 

@@ -144,7 +144,7 @@ struct DFT {
 };
 
 // Two-level split of a line length N = N1 * N2 used by the shared-memory
-// line FFT: stage A runs N2 register DFTs of length N1, stage B N1 of length N2.
+// line FFT (see fft_smem.cuh).
 template <int N> struct LineSplit;
 template <> struct LineSplit<8>   { static constexpr int N1 = 8,  N2 = 1; };
 template <> struct LineSplit<12>  { static constexpr int N1 = 12, N2 = 1; };

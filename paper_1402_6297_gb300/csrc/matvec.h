@@ -10,6 +10,18 @@ namespace nfs {
 template <typename R>
 struct MatView;
 
+// Strides between the problems of a batched launch (P problems of one grid,
+// stored back to back): elements for vectors / fields / tables, reals for the
+// material, ints for the skip flags, doubles for the per-problem CG state.
+struct BatchStrides {
+  long long su = 0;      // u, Au, cg_r
+  long long sfld = 0;    // fld
+  long long smat = 0;    // inv_phi, gam, inv_mu
+  long long sstate = 0;  // cg_beta, dot_part
+  int slam = 0;          // lam
+  int sskip = 0;         // skip
+};
+
 template <typename R>
 struct MatvecArgs {
   const cplx<R>* u;       // 4n, spectral
@@ -27,6 +39,13 @@ struct MatvecArgs {
   R alpha, beta;
   const int* skip;        // device flag: when nonzero every pass returns at once
   cudaStream_t stream;
+  // CG fusion (both optional, nullptr when unused):
+  const cplx<R>* cg_r;    // pass 1 first forms u = cg_r + (*cg_beta) u in place
+  const double* cg_beta;
+  double* dot_part;       // pass 3 writes one partial of Re(u^* A u) per CTA
+  // batching: P problems of this grid in one launch (P = 1 for one problem)
+  int P;
+  BatchStrides bs;
 };
 
 // Largest dynamic shared memory a CTA may request on sm_103a.

@@ -65,13 +65,13 @@ template <typename R, int NX>
 static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
   if constexpr (plane_fits<R, NX>()) {
     constexpr int NT = plane_threads(NX);
-    dim3 grid(3, 2, a.n3);
+    dim3 grid(3, 2, a.n3 * (a.P > 0 ? a.P : 1));
     if (which == 1) {
       k_pass1_assemble_ifft_xy<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
-          a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip);
+          a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.bs);
     } else {
       k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
-          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip);
+          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.u, a.dot_part, a.bs);
     }
     return cudaGetLastError();
   } else {
@@ -86,8 +86,9 @@ static cudaError_t z_launch(const MatvecArgs<R>& a) {
   const int ncols = a.n1 * a.n2;
   MatView<R> mv{a.inv_phi, a.gam, a.inv_mu, a.kind, a.ax_a, a.ax_b, (long long)ncols * a.n3};
   const R inv_n = (R)(1.0 / ((double)ncols * (double)a.n3));
-  k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))><<<ncols / TX, NT, z_smem<R, N3>(), a.stream>>>(a.fld, mv, a.tw3, ncols, inv_n,
-                                                                                 a.skip);
+  k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))>
+      <<<(ncols / TX) * (a.P > 0 ? a.P : 1), NT, z_smem<R, N3>(), a.stream>>>(a.fld, mv, a.tw3, ncols, inv_n, a.skip,
+                                                                             a.bs);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@
 #include <cooperative_groups.h>
 
 #include "fft_smem.cuh"
+#include "matvec.h"
 
 namespace nfs {
 namespace cg = cooperative_groups;
@@ -106,6 +107,25 @@ __device__ __forceinline__ void burst_store(C* __restrict__ dst, Get get) {
   }
 }
 
+// Sum of one double per thread over the block (result valid in thread 0).
+template <int NT>
+__device__ __forceinline__ double block_sum_dbl(double v) {
+  __shared__ double sh[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < NT / 32 ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  __syncthreads();
+  return r;
+}
+
 template <typename R>
 struct Basis {
   cplx<R> c[3];
@@ -145,10 +165,11 @@ __device__ __forceinline__ int third_bound(int r) {
 
 template <typename R, int NX, int NY, int NT, int MINB>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
-k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fld,
+k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
                          const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                          const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
-                         const int* __restrict__ skip) {
+                         const int* __restrict__ skip, const cplx<R>* __restrict__ cg_r,
+                         const double* __restrict__ cg_beta, BatchStrides bs) {
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
@@ -158,10 +179,18 @@ k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fl
   C* stx = plane + NY * PITCH;
   C* sty = stx + NX;
   cg::cluster_group cl = cg::this_cluster();
-  if (skip != nullptr && *skip) return;  // uniform across the grid
+  const int prob = blockIdx.z / n3;
+  if (skip != nullptr && skip[(long long)prob * bs.sskip]) return;  // uniform across the cluster
   const int rank = (int)cl.block_rank();
   const int grp = blockIdx.y;
-  const int i3 = blockIdx.z;
+  const int i3 = blockIdx.z % n3;
+  u += prob * bs.su;
+  fld += prob * bs.sfld;
+  lam += (long long)prob * bs.slam;
+  if (cg_r != nullptr) {
+    cg_r += prob * bs.su;
+    cg_beta += prob * bs.sstate;
+  }
   for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
 
@@ -180,8 +209,33 @@ k_pass1_assemble_ifft_xy(const cplx<R>* __restrict__ u, cplx<R>* __restrict__ fl
   for (int b = 0; b < PER; ++b) {
     const int v = b * NT + (int)threadIdx.x;
     if (v < nv) {
-      ra[b] = __ldg(reinterpret_cast<const V*>(ua) + v);
-      rb[b] = __ldg(reinterpret_cast<const V*>(ub) + v);
+      ra[b] = reinterpret_cast<const V*>(ua)[v];
+      rb[b] = reinterpret_cast<const V*>(ub)[v];
+    }
+  }
+  if (cg_r != nullptr) {
+    // CG direction update fused into the load: u = r + beta u, stored back
+    const R bt = (R)*cg_beta;
+    const long long off = (2 * grp) * n + (long long)i3 * NE + e0;
+    const V* rva = reinterpret_cast<const V*>(cg_r + off);
+    const V* rvb = reinterpret_cast<const V*>(cg_r + off + n);
+    V* wa = reinterpret_cast<V*>(const_cast<C*>(ua));
+    V* wb = reinterpret_cast<V*>(const_cast<C*>(ub));
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+      const int v = b * NT + (int)threadIdx.x;
+      if (v < nv) {
+        const V qa = __ldg(rva + v), qb = __ldg(rvb + v);
+        if constexpr (EPV == 2) {
+          ra[b] = make_float4(qa.x + bt * ra[b].x, qa.y + bt * ra[b].y, qa.z + bt * ra[b].z, qa.w + bt * ra[b].w);
+          rb[b] = make_float4(qb.x + bt * rb[b].x, qb.y + bt * rb[b].y, qb.z + bt * rb[b].z, qb.w + bt * rb[b].w);
+        } else {
+          ra[b] = mk(qa.x + bt * ra[b].x, qa.y + bt * ra[b].y);
+          rb[b] = mk(qb.x + bt * rb[b].x, qb.y + bt * rb[b].y);
+        }
+        wa[v] = ra[b];
+        wb[v] = rb[b];
+      }
     }
   }
   const C a3 = lam[NX + NY + i3];
@@ -295,7 +349,7 @@ __device__ __forceinline__ void material_apply(const MatView<R>& m, long long v,
 template <typename R, int N3, int TX, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __restrict__ twz, int ncols,
-                   R inv_n, const int* __restrict__ skip) {
+                   R inv_n, const int* __restrict__ skip, BatchStrides bs) {
   using C = cplx<R>;
   using V = typename Vec16<C>::type;
   constexpr int EPV = 16 / (int)sizeof(C);
@@ -306,9 +360,15 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* stw = buf + N3 * PITCH;
-  if (skip != nullptr && *skip) return;
+  const int tiles = ncols / TX;
+  const int prob = blockIdx.x / tiles;
+  if (skip != nullptr && skip[(long long)prob * bs.sskip]) return;
+  fld += prob * bs.sfld;
+  mat.inv_phi += prob * bs.smat;
+  mat.gam += prob * bs.smat;
+  if (mat.inv_mu) mat.inv_mu += prob * bs.smat;
   for (int i = threadIdx.x; i < N3; i += NT) stw[i] = twz[i];
-  const int col0 = blockIdx.x * TX;
+  const int col0 = (blockIdx.x % tiles) * TX;
   const long long n = (long long)ncols * N3;
   {
     constexpr int PER = (NV + NT - 1) / NT;
@@ -378,7 +438,8 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au,
                        const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                        const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
-                       const int* __restrict__ skip) {
+                       const int* __restrict__ skip, const cplx<R>* __restrict__ u, double* __restrict__ dot_part,
+                       BatchStrides bs) {
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
@@ -388,10 +449,18 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   C* stx = plane + NY * PITCH;
   C* sty = stx + NX;
   cg::cluster_group cl = cg::this_cluster();
-  if (skip != nullptr && *skip) return;
+  const int prob = blockIdx.z / n3;
+  if (skip != nullptr && skip[(long long)prob * bs.sskip]) return;
   const int rank = (int)cl.block_rank();
   const int grp = blockIdx.y;
-  const int i3 = blockIdx.z;
+  const int i3 = blockIdx.z % n3;
+  fld += prob * bs.sfld;
+  Au += prob * bs.su;
+  lam += (long long)prob * bs.slam;
+  if (dot_part != nullptr) {
+    u += prob * bs.su;
+    dot_part += prob * bs.sstate;
+  }
   for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
   const C* in = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
@@ -410,6 +479,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   C* o1 = o0 + n;
   const C a3 = lam[NX + NY + i3];
   const int e0 = third_bound<NE>(rank), e1 = third_bound<NE>(rank + 1);
+  double dot_acc = 0.0;
   // element pairs (i1 even) so that the two outputs leave as 16-byte stores
   for (int ep = e0 / 2 + threadIdx.x; ep < e1 / 2; ep += NT) {
     C r0[2], r1[2];
@@ -440,6 +510,22 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
       o1[2 * ep] = r1[0];
       o1[2 * ep + 1] = r1[1];
     }
+    if (dot_part != nullptr) {
+      // Re(u^* A u) over this CTA's outputs (the CG curvature p^* A p)
+      const C* u0 = u + (2 * grp) * n + (long long)i3 * NE;
+      const C* u1 = u0 + n;
+      R s = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const C pa = u0[2 * ep + h], pb = u1[2 * ep + h];
+        s += pa.x * r0[h].x + pa.y * r0[h].y + pb.x * r1[h].x + pb.y * r1[h].y;
+      }
+      dot_acc += (double)s;
+    }
+  }
+  if (dot_part != nullptr) {
+    const double tot = block_sum_dbl<NT>(dot_acc);
+    if (threadIdx.x == 0) dot_part[((long long)i3 * 2 + blockIdx.y) * 3 + blockIdx.x] = tot;
   }
   cl.sync();  // keep this CTA's plane alive until the cluster finished reading it
 }

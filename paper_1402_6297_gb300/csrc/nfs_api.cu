@@ -1,60 +1,97 @@
 // libnfs C ABI: context setup, A_r and B_r products, CG (FP64 and mixed
 // precision with FP64 refinement), thick-restart invert Lanczos on the
-// HHPD-NFGEP, and the eigenvalue gradient.  See include/nfs.h.
+// HHPD-NFGEP, the eigenvalue gradient, and batches of independent problems.
+// See include/nfs.h.
+//
+// A context holds P >= 1 problems that share one grid (different k-points
+// and media).  Every kernel serves all P problems in one launch (the problem
+// index is a grid dimension), and the solvers run the P problems in lock-step
+// with per-problem scalars on the host; problems that have converged are
+// masked out.  nfs_setup makes a context with P = 1; nfs_setup_batch groups
+// a batch by grid into such contexts and drives each from its own host thread
+// and stream, so different grid sizes overlap on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
+#include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/nfs.h"
 #include "blas_kernels.cuh"
+#include "host_eig.h"
 #include "matvec.h"
 
 using nfs::CGState;
 using nfs::kRedBlocks;
 using nfs::kRedThreads;
 
+namespace {
+struct GraphEntry {
+  const void* key[5];
+  cudaGraphExec_t exec;
+};
+}  // namespace
+
 struct nfs_ctx {
-  int n1 = 0, n2 = 0, n3 = 0;
+  int n1 = 0, n2 = 0, n3 = 0, nl = 0;
   long long n = 0, N = 0;  // voxels, 4n
-  double kdota[3] = {0, 0, 0};
+  int P = 1;               // problems in this context
   double delta[3] = {0, 0, 0};
   nfs_options opt{};
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // caller's stream
+  cudaStream_t work = nullptr;    // the library's own stream (CG and Lanczos; graph capture)
+  cudaEvent_t ev = nullptr;
   int kind = 0, ax_a = 0, ax_b = 1;
   bool has_mu = false;
-  // tables
+  long long gam_len = 0, mat_len = 0;
+  // tables (per problem: stride nl) and twiddles (shared)
   double2* lam64 = nullptr;
   float2* lam32 = nullptr;
   double2* tw64[3] = {nullptr, nullptr, nullptr};
   float2* tw32[3] = {nullptr, nullptr, nullptr};
-  // material: inv_phi [3n] | gam [3n or n] | inv_mu [3n] (optional)
+  // material, per problem (stride mat_len): inv_phi [3n] | gam [3n or n] | inv_mu [3n]
   double* mat64 = nullptr;
   float* mat32 = nullptr;
-  long long gam_len = 0;
-  // workspaces
-  void* fld = nullptr;  // 6n complex128 (complex64 uses the first half)
+  // workspaces, per problem
+  void* fld = nullptr;  // 6n complex128 each (complex64 uses 12n entries of it)
   double2 *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *Ap64 = nullptr, *t64 = nullptr, *t64b = nullptr;
   float2 *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
   CGState* st = nullptr;
-  CGState* st_host = nullptr;  // pinned mirror (done/it/status/rr)
+  CGState* st_host = nullptr;  // pinned mirror of the scalar part
+  // small per-problem arrays (device + pinned host): tolerances, scales, flags
+  double* d_small = nullptr;
+  double* h_small = nullptr;
+  int* d_flags = nullptr;
+  int* h_flags = nullptr;
   double* dscratch = nullptr;  // reductions
   size_t dscratch_len = 0;
   double* hscratch = nullptr;  // pinned
   size_t hscratch_len = 0;
-  // Lanczos basis
+  // Lanczos basis (FP64) and its complex64 shadows; problem stride vcap * N
   double2* V = nullptr;
   double2* MV = nullptr;
+  float2* V32 = nullptr;
+  float2* MV32 = nullptr;
+  float2* w32 = nullptr;
   int vcap = 0;
   double* dY = nullptr;  // rotation coefficients
-  int dY_len = 0;
+  size_t dY_len = 0;
+  std::vector<GraphEntry> graphs;
   long long bytes = 0;
   long long mv32 = 0, mv64 = 0;
+};
+
+struct nfs_batch {
+  std::vector<nfs_ctx*> classes;
+  std::vector<std::pair<int, int>> where;  // problem -> (class, index in class)
 };
 
 namespace {
@@ -72,6 +109,12 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);            \
   } while (0)
 
+#define TRY(call)                 \
+  do {                            \
+    int r_ = (call);              \
+    if (r_ != NFS_OK) return r_;  \
+  } while (0)
+
 template <typename T>
 int dalloc(nfs_ctx* c, T** p, size_t count) {
   size_t bytes = count * sizeof(T);
@@ -86,12 +129,6 @@ int dalloc(nfs_ctx* c, T** p, size_t count) {
   return NFS_OK;
 }
 
-#define TRY(call)                 \
-  do {                            \
-    int r_ = (call);              \
-    if (r_ != NFS_OK) return r_;  \
-  } while (0)
-
 bool size_ok(int s) {
   switch (s) {
     case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: return true;
@@ -101,10 +138,21 @@ bool size_ok(int s) {
 
 int grid_blocks(long long N, int threads) {
   long long b = (N + threads - 1) / threads;
-  return (int)std::min<long long>(b, 152LL * 16);
+  return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
 }
 
 // --- matvec -------------------------------------------------------------
+
+nfs::BatchStrides strides(const nfs_ctx* c, long long sfld) {
+  nfs::BatchStrides b;
+  b.su = c->N;
+  b.sfld = sfld;
+  b.smat = c->mat_len;
+  b.sstate = nfs::kStateDoubles;
+  b.slam = c->nl;
+  b.sskip = nfs::kStateInts;
+  return b;
+}
 
 template <typename R>
 nfs::MatvecArgs<R> margs(nfs_ctx* c, const nfs::cplx<R>* u, nfs::cplx<R>* Au, const int* skip);
@@ -118,6 +166,8 @@ nfs::MatvecArgs<double> margs<double>(nfs_ctx* c, const double2* u, double2* Au,
   a.kind = c->kind; a.ax_a = c->ax_a; a.ax_b = c->ax_b;
   a.n1 = c->n1; a.n2 = c->n2; a.n3 = c->n3; a.alpha = c->opt.alpha; a.beta = c->opt.beta;
   a.skip = skip; a.stream = c->stream;
+  a.P = c->P;
+  a.bs = strides(c, 6 * c->n);
   return a;
 }
 
@@ -130,208 +180,26 @@ nfs::MatvecArgs<float> margs<float>(nfs_ctx* c, const float2* u, float2* Au, con
   a.kind = c->kind; a.ax_a = c->ax_a; a.ax_b = c->ax_b;
   a.n1 = c->n1; a.n2 = c->n2; a.n3 = c->n3; a.alpha = (float)c->opt.alpha; a.beta = (float)c->opt.beta;
   a.skip = skip; a.stream = c->stream;
+  a.P = c->P;
+  a.bs = strides(c, 12 * c->n);  // the complex128-sized workspace holds 12 n complex64 per problem
   return a;
 }
 
+// P products (problem p's vectors at u + p N); skip (optional): problem p is
+// skipped when skip[p * sskip] is nonzero.
 template <typename R>
-int matvec(nfs_ctx* c, const nfs::cplx<R>* u, nfs::cplx<R>* Au, const int* skip = nullptr) {
-  cudaError_t e = nfs::matvec_launch<R>(margs<R>(c, u, Au, skip));
+int matvec(nfs_ctx* c, cudaStream_t s, const nfs::cplx<R>* u, nfs::cplx<R>* Au, const int* skip = nullptr,
+           int sskip = 0) {
+  nfs::MatvecArgs<R> a = margs<R>(c, u, Au, skip);
+  a.stream = s;
+  a.bs.sskip = sskip;
+  cudaError_t e = nfs::matvec_launch<R>(a);
   if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
-  if (sizeof(R) == 4) c->mv32++; else c->mv64++;
+  if (sizeof(R) == 4) c->mv32 += c->P; else c->mv64 += c->P;
   return NFS_OK;
 }
 
-// --- reductions -------------------------------------------------------------
-
-template <typename C>
-int dot_re(nfs_ctx* c, const C* x, const C* y, double* out) {
-  nfs::k_dot_re<C><<<kRedBlocks, kRedThreads, 0, c->stream>>>(x, y, c->N, c->dscratch, nullptr);
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(c->hscratch, c->dscratch, kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  double s = 0.0;
-  for (int i = 0; i < kRedBlocks; ++i) s += c->hscratch[i];
-  *out = s;
-  return NFS_OK;
-}
-
-// --- CG ---------------------------------------------------------------------
-
-constexpr int kCgChunk = 8;
-
-// Runs CG from the state r = b - A x (already formed), p scratch.  tol2 is the
-// absolute threshold on r^* r.  Returns NFS_OK / NFS_E* and the iteration count.
-template <typename R>
-int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::cplx<R>* Ap, double tol2, int maxit,
-           int* iters, int* status) {
-  using C = nfs::cplx<R>;
-  const long long N = c->N;
-  CK(cudaMemcpyAsync(p, r, N * sizeof(C), cudaMemcpyDeviceToDevice, c->stream));
-  nfs::k_dot_re<C><<<kRedBlocks, kRedThreads, 0, c->stream>>>(r, r, N, c->st->part_a, nullptr);
-  nfs::k_cg_init<<<1, kRedThreads, 0, c->stream>>>(c->st, tol2, maxit);
-  CK(cudaGetLastError());
-  int done = 0;
-  const int* skip = &c->st->done;
-  for (;;) {
-    for (int i = 0; i < kCgChunk; ++i) {
-      TRY(matvec<R>(c, p, Ap, skip));
-      nfs::k_dot_re<C><<<kRedBlocks, kRedThreads, 0, c->stream>>>(p, Ap, N, c->st->part_a, skip);
-      nfs::k_cg_alpha<<<1, kRedThreads, 0, c->stream>>>(c->st);
-      nfs::k_cg_update_xr<C><<<kRedBlocks, kRedThreads, 0, c->stream>>>(x, r, p, Ap, N, c->st);
-      nfs::k_cg_beta<<<1, kRedThreads, 0, c->stream>>>(c->st);
-      nfs::k_cg_update_p<C><<<kRedBlocks, kRedThreads, 0, c->stream>>>(p, r, N, c->st);
-      CK(cudaGetLastError());
-    }
-    CK(cudaMemcpyAsync(c->st_host, c->st, offsetof(CGState, part_a), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    done = c->st_host->done;
-    if (done) break;
-  }
-  *iters = c->st_host->it;
-  *status = c->st_host->status;
-  return NFS_OK;
-}
-
-int launch_sub64(nfs_ctx* c, const double2* a, const double2* b, double2* y) {
-  nfs::k_sub<double2><<<grid_blocks(c->N, 256), 256, 0, c->stream>>>(a, b, y, c->N);
-  CK(cudaGetLastError());
-  return NFS_OK;
-}
-
-// FP64 CG on A_r x = b (complex128 throughout).
-int solve_fp64(nfs_ctx* c, const double2* b, double2* x, bool x_zero, nfs_solve_info* info) {
-  double bb;
-  TRY(dot_re(c, b, b, &bb));
-  if (bb == 0.0) {
-    CK(cudaMemsetAsync(x, 0, c->N * sizeof(double2), c->stream));
-    if (info) *info = nfs_solve_info{0, 0, 0.0, NFS_OK};
-    return NFS_OK;
-  }
-  if (x_zero) {
-    CK(cudaMemsetAsync(x, 0, c->N * sizeof(double2), c->stream));
-    CK(cudaMemcpyAsync(c->r64, b, c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  } else {
-    TRY(matvec<double>(c, x, c->Ap64));
-    TRY(launch_sub64(c, b, c->Ap64, c->r64));
-  }
-  int it = 0, st = 0;
-  const double tol = c->opt.cg_tol;
-  TRY(cg_run<double>(c, x, c->r64, c->p64, c->Ap64, tol * tol * bb, c->opt.cg_maxit, &it, &st));
-  if (info) {
-    info->iterations = it;
-    info->refinements = 0;
-    info->rel_residual = std::sqrt(std::max(c->st_host->rr, 0.0) / bb);
-    info->status = st;
-  }
-  return st;
-}
-
-// Mixed precision: complex64 CG inner solves inside FP64 iterative refinement
-// r = b - A_r x evaluated with the complex128 product.
-int solve_mixed(nfs_ctx* c, const double2* b, double2* x, bool x_zero, nfs_solve_info* info) {
-  double bb;
-  TRY(dot_re(c, b, b, &bb));
-  if (bb == 0.0) {
-    CK(cudaMemsetAsync(x, 0, c->N * sizeof(double2), c->stream));
-    if (info) *info = nfs_solve_info{0, 0, 0.0, NFS_OK};
-    return NFS_OK;
-  }
-  if (x_zero) {
-    CK(cudaMemsetAsync(x, 0, c->N * sizeof(double2), c->stream));
-    CK(cudaMemcpyAsync(c->r64, b, c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  } else {
-    TRY(matvec<double>(c, x, c->Ap64));
-    TRY(launch_sub64(c, b, c->Ap64, c->r64));
-  }
-  const double tol2 = c->opt.cg_tol * c->opt.cg_tol * bb;
-  int total_it = 0, refines = 0, status = NFS_OK;
-  double rr = 0.0;
-  const int nb = grid_blocks(c->N, 256);
-  for (;;) {
-    TRY(dot_re(c, c->r64, c->r64, &rr));
-    if (!(rr == rr)) { status = NFS_EBREAKDOWN; break; }
-    if (rr <= tol2) break;
-    if (refines >= c->opt.max_refine) { status = NFS_ENOCONV; break; }
-    const double rn = std::sqrt(rr);
-    nfs::k_demote<<<nb, 256, 0, c->stream>>>(c->r64, 1.0 / rn, c->r32, c->N);
-    CK(cudaGetLastError());
-    CK(cudaMemsetAsync(c->x32, 0, c->N * sizeof(float2), c->stream));
-    int it = 0, st = 0;
-    const double itol = c->opt.inner_tol;
-    TRY(cg_run<float>(c, c->x32, c->r32, c->p32, c->Ap32, itol * itol, c->opt.cg_maxit, &it, &st));
-    total_it += it;
-    nfs::k_axpy_promote<<<nb, 256, 0, c->stream>>>(x, rn, c->x32, c->N);
-    CK(cudaGetLastError());
-    TRY(matvec<double>(c, x, c->Ap64));
-    TRY(launch_sub64(c, b, c->Ap64, c->r64));
-    ++refines;
-    if (st == NFS_EBREAKDOWN) { status = st; break; }
-  }
-  if (info) {
-    info->iterations = total_it;
-    info->refinements = refines;
-    info->rel_residual = std::sqrt(std::max(rr, 0.0) / bb);
-    info->status = status;
-  }
-  return status;
-}
-
-int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, nfs_solve_info* info) {
-  if (c->opt.precision == NFS_PREC_MIXED) return solve_mixed(c, b, x, x_zero, info);
-  return solve_fp64(c, b, x, x_zero, info);
-}
-
-// --- host symmetric eigensolver (cyclic Jacobi) ------------------------------
-
-// A (m x m, row-major, symmetric) -> eigenvalues w (ascending) and
-// eigenvectors as the columns of Z (row-major m x m).
-void jacobi_eig(int m, std::vector<double> A, std::vector<double>& w, std::vector<double>& Z) {
-  Z.assign((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
-  auto a = [&](int i, int j) -> double& { return A[(size_t)i * m + j]; };
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < m; ++i) {
-      diag += a(i, i) * a(i, i);
-      for (int j = i + 1; j < m; ++j) off += a(i, j) * a(i, j);
-    }
-    if (off <= 1e-32 * diag || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p) {
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = a(p, q);
-        if (std::fabs(apq) < 1e-300) continue;
-        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
-        for (int k = 0; k < m; ++k) {  // columns p, q
-          const double akp = a(k, p), akq = a(k, q);
-          a(k, p) = cs * akp - sn * akq;
-          a(k, q) = sn * akp + cs * akq;
-        }
-        for (int k = 0; k < m; ++k) {  // rows p, q
-          const double apk = a(p, k), aqk = a(q, k);
-          a(p, k) = cs * apk - sn * aqk;
-          a(q, k) = sn * apk + cs * aqk;
-        }
-        for (int k = 0; k < m; ++k) {
-          const double zkp = Z[(size_t)k * m + p], zkq = Z[(size_t)k * m + q];
-          Z[(size_t)k * m + p] = cs * zkp - sn * zkq;
-          Z[(size_t)k * m + q] = sn * zkp + cs * zkq;
-        }
-      }
-    }
-  }
-  std::vector<int> idx(m);
-  for (int i = 0; i < m; ++i) idx[i] = i;
-  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return a(i, i) < a(j, j); });
-  w.resize(m);
-  std::vector<double> Zs((size_t)m * m);
-  for (int c2 = 0; c2 < m; ++c2) {
-    w[c2] = a(idx[c2], idx[c2]);
-    for (int k = 0; k < m; ++k) Zs[(size_t)k * m + c2] = Z[(size_t)k * m + idx[c2]];
-  }
-  Z.swap(Zs);
-}
+// --- scratch ---------------------------------------------------------------
 
 int ensure_scratch(nfs_ctx* c, size_t dlen) {
   if (c->dscratch_len < dlen) {
@@ -349,81 +217,898 @@ int ensure_scratch(nfs_ctx* c, size_t dlen) {
   return NFS_OK;
 }
 
-// Lanczos scratch layout in dscratch (mcap = basis capacity):
-//   [0, P)            per-block partial dots, P = kRedBlocks * 2 * mcap
-//   [P, P + 2 mcap)   finished dots
-//   [P + 2 mcap, ...) coefficients for the update
-size_t lanczos_scratch_len(int mcap) { return (size_t)kRedBlocks * 2 * mcap + 4 * (size_t)mcap + 64; }
-
-// c = V[0:m]^* w (complex, m entries) on the host
-int multi_dot(nfs_ctx* c, const double2* V, int m, const double2* w, std::vector<double>& out) {
-  double* part = c->dscratch;
-  double* fin = c->dscratch + (size_t)kRedBlocks * 2 * c->vcap;
-  nfs::k_multi_dot<kRedThreads><<<kRedBlocks, kRedThreads, 0, c->stream>>>(V, m, w, c->N, part);
-  nfs::k_multi_dot_finish<<<m, kRedThreads, 0, c->stream>>>(part, m, kRedBlocks, fin);
+// Re(x_p^* y_p) for every problem, on the host
+template <typename C>
+int dots_re(nfs_ctx* c, cudaStream_t s, const C* x, const C* y, std::vector<double>& out) {
+  nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(x, y, c->N, c->dscratch, kRedBlocks, nullptr, 0);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)m * 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  out.assign(c->hscratch, c->hscratch + 2 * m);
+  CK(cudaMemcpyAsync(c->hscratch, c->dscratch, (size_t)kRedBlocks * c->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out.assign(c->P, 0.0);
+  for (int p = 0; p < c->P; ++p) {
+    double t = 0.0;
+    for (int i = 0; i < kRedBlocks; ++i) t += c->hscratch[(size_t)p * kRedBlocks + i];
+    out[p] = t;
+  }
   return NFS_OK;
 }
 
-int multi_axpy(nfs_ctx* c, double2* w, double2* Mw, const double2* V, const double2* MV, int m,
-               const std::vector<double>& coef) {
-  double* dcoef = c->dscratch + (size_t)kRedBlocks * 2 * c->vcap + 2 * (size_t)c->vcap;
-  std::memcpy(c->hscratch, coef.data(), coef.size() * sizeof(double));
-  CK(cudaMemcpyAsync(dcoef, c->hscratch, coef.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  nfs::k_multi_axpy<<<grid_blocks(c->N, 256), 256, 0, c->stream>>>(w, Mw, V, MV, dcoef, m, c->N);
+// Layout of d_small (doubles): [0, P) tolerances, [P, 2P) and [2P, 3P) scales;
+// of d_flags (ints): [0, P) active problems, [P, 2P) a second mask.
+constexpr int kSmallSlots = 3;
+constexpr int kFlagSlots = 2;
+
+// upload v to c->d_small + off through the pinned mirror
+int put_small(nfs_ctx* c, cudaStream_t s, int off, const std::vector<double>& v) {
+  std::memcpy(c->h_small + off, v.data(), v.size() * sizeof(double));
+  CK(cudaMemcpyAsync(c->d_small + off, c->h_small + off, v.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  return NFS_OK;
+}
+
+int put_flags(nfs_ctx* c, cudaStream_t s, int off, const std::vector<int>& v) {
+  std::memcpy(c->h_flags + off, v.data(), v.size() * sizeof(int));
+  CK(cudaMemcpyAsync(c->d_flags + off, c->h_flags + off, v.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  return NFS_OK;
+}
+
+// --- CG ---------------------------------------------------------------------
+
+constexpr int kCgChunk = 8;
+// Lanczos vectors are kept orthogonal in the A_r inner product to within this
+// level (about sqrt of the FP64 unit round-off), which keeps the Ritz values
+// accurate to FP64 round-off (semi-orthogonality).
+constexpr double kSemiOrthogonality = 1e-8;
+
+// Enqueue kCgChunk iterations for all problems: pass 1 (which first forms
+// p = r + beta p), passes 2 and 3 (pass 3 also emits the p^* A p partials),
+// the x/r update (which forms alpha itself) and the beta kernel.
+template <typename R>
+cudaError_t enqueue_cg_chunk(nfs_ctx* c, cudaStream_t s, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p,
+                             nfs::cplx<R>* Ap) {
+  using C = nfs::cplx<R>;
+  nfs::MatvecArgs<R> a = margs<R>(c, p, Ap, &c->st->done);
+  a.stream = s;
+  a.cg_r = r;
+  a.cg_beta = &c->st->beta;
+  a.dot_part = c->st->part_a;
+  for (int i = 0; i < kCgChunk; ++i) {
+    cudaError_t e = nfs::matvec_launch<R>(a);
+    if (e != cudaSuccess) return e;
+    nfs::k_cg_update_xr<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(x, r, p, Ap, c->N, c->st);
+    nfs::k_cg_beta<<<c->P, kRedThreads, 0, s>>>(c->st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// The chunk as a CUDA graph, captured once per (precision, buffers) on the
+// context's work stream and replayed: one launch per chunk instead of
+// 5 kCgChunk kernel launches.
+template <typename R>
+int cg_chunk_graph(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::cplx<R>* Ap,
+                   cudaGraphExec_t* out) {
+  const void* key[5] = {x, r, p, Ap, (const void*)(uintptr_t)sizeof(R)};
+  for (const GraphEntry& g : c->graphs)
+    if (std::equal(key, key + 5, g.key)) {
+      *out = g.exec;
+      return NFS_OK;
+    }
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_cg_chunk<R>(c, c->work, x, r, p, Ap);
+  cudaError_t e2 = cudaStreamEndCapture(c->work, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "cg capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  GraphEntry g;
+  std::copy(key, key + 5, g.key);
+  g.exec = exec;
+  c->graphs.push_back(g);
+  *out = exec;
+  return NFS_OK;
+}
+
+// CG from the state r = b - A x (already formed) for every problem, on the
+// work stream; tol2 the absolute thresholds on r^* r (+inf skips a problem).
+// Iterations run in graph-replayed chunks; every kernel returns at once after
+// its problem's device `done` flag is set, and the host reads the flags
+// between chunks.
+template <typename R>
+int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::cplx<R>* Ap,
+           const std::vector<double>& tol2, int maxit, std::vector<int>& iters, std::vector<int>& status) {
+  using C = nfs::cplx<R>;
+  cudaStream_t s = c->work;
+  CK(cudaMemsetAsync(p, 0, c->P * c->N * sizeof(C), s));  // with beta = 0 the first pass 1 sets p = r
+  nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(r, r, c->N, c->st->part_a, nfs::kStateDoubles,
+                                                                   nullptr, 0);
+  TRY(put_small(c, s, 0, tol2));
+  nfs::k_cg_init<<<c->P, kRedThreads, 0, s>>>(c->st, c->d_small, maxit, 6 * c->n3);
   CK(cudaGetLastError());
-  // the host scratch is reused by the next call: make sure the copy consumed it
-  CK(cudaStreamSynchronize(c->stream));
+  cudaGraphExec_t exec = nullptr;
+  TRY(cg_chunk_graph<R>(c, x, r, p, Ap, &exec));
+  const size_t head = offsetof(CGState, part_a);
+  for (;;) {
+    CK(cudaGraphLaunch(exec, s));
+    CK(cudaMemcpy2DAsync(c->st_host, sizeof(CGState), c->st, sizeof(CGState), head, c->P, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int q = 0; q < c->P; ++q) all = all && c->st_host[q].done;
+    if (all) break;
+  }
+  iters.resize(c->P);
+  status.resize(c->P);
+  for (int q = 0; q < c->P; ++q) {
+    iters[q] = c->st_host[q].it;
+    status[q] = c->st_host[q].status;
+    // one product per iteration that ran (launches after convergence are empty)
+    if (sizeof(R) == 4) c->mv32 += iters[q]; else c->mv64 += iters[q];
+  }
+  return NFS_OK;
+}
+
+int sub64(nfs_ctx* c, cudaStream_t s, const double2* a, const double2* b, double2* y) {
+  const long long tot = c->P * c->N;
+  nfs::k_sub<double2><<<grid_blocks(tot, 256), 256, 0, s>>>(a, b, y, tot);
+  CK(cudaGetLastError());
+  return NFS_OK;
+}
+
+// Solve A_r x_p = b_p for every problem p with active[p] (b, x: P x N, on the
+// work stream).  FP64 contexts run complex128 CG; MIXED contexts run complex64
+// CG inside FP64 iterative refinement (the residual r = b - A_r x with the
+// complex128 product, scaled to unit norm, demoted; x += |r| d).
+struct SolveOut {
+  std::vector<int> iters, refines, status;
+  std::vector<double> relres;
+};
+
+int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, const std::vector<int>& active, SolveOut& so) {
+  cudaStream_t s = c->work;
+  const int P = c->P;
+  const long long tot = P * c->N;
+  std::vector<double> bb;
+  TRY(dots_re(c, s, b, b, bb));
+  so.iters.assign(P, 0);
+  so.refines.assign(P, 0);
+  so.status.assign(P, NFS_OK);
+  so.relres.assign(P, 0.0);
+  if (x_zero) {
+    CK(cudaMemsetAsync(x, 0, tot * sizeof(double2), s));
+    CK(cudaMemcpyAsync(c->r64, b, tot * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  } else {
+    TRY(matvec<double>(c, s, x, c->Ap64));
+    TRY(sub64(c, s, b, c->Ap64, c->r64));
+  }
+  const double tol = c->opt.cg_tol;
+  std::vector<int> need(P);
+  for (int q = 0; q < P; ++q) need[q] = active[q] && bb[q] > 0.0;
+  if (c->opt.precision != NFS_PREC_MIXED) {
+    std::vector<double> tol2(P);
+    for (int q = 0; q < P; ++q) tol2[q] = need[q] ? tol * tol * bb[q] : INFINITY;
+    std::vector<int> it, st;
+    TRY(cg_run<double>(c, x, c->r64, c->p64, c->Ap64, tol2, c->opt.cg_maxit, it, st));
+    for (int q = 0; q < P; ++q) {
+      if (!need[q]) continue;
+      so.iters[q] = it[q];
+      so.status[q] = st[q];
+      so.relres[q] = std::sqrt(std::max(c->st_host[q].rr, 0.0) / bb[q]);
+    }
+    return NFS_OK;
+  }
+  // mixed precision
+  const int nb = grid_blocks(tot, 256);
+  std::vector<double> rr;
+  std::vector<int> live(need);
+  for (;;) {
+    TRY(dots_re(c, s, c->r64, c->r64, rr));
+    bool any = false;
+    std::vector<double> inv(P, 0.0), nrm(P, 0.0), itol2(P, INFINITY);
+    std::vector<int> skip(P, 1);
+    for (int q = 0; q < P; ++q) {
+      if (!live[q]) continue;
+      so.relres[q] = std::sqrt(std::max(rr[q], 0.0) / bb[q]);
+      if (!(rr[q] == rr[q])) { so.status[q] = NFS_EBREAKDOWN; live[q] = 0; continue; }
+      if (rr[q] <= tol * tol * bb[q]) { live[q] = 0; continue; }
+      if (so.refines[q] >= c->opt.max_refine) { so.status[q] = NFS_ENOCONV; live[q] = 0; continue; }
+      any = true;
+      nrm[q] = std::sqrt(rr[q]);
+      inv[q] = 1.0 / nrm[q];
+      itol2[q] = c->opt.inner_tol * c->opt.inner_tol;
+      skip[q] = 0;
+    }
+    if (!any) break;
+    TRY(put_small(c, s, P, inv));
+    nfs::k_demote<<<nb, 256, 0, s>>>(c->r64, c->d_small + P, c->r32, c->N, tot);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(c->x32, 0, tot * sizeof(float2), s));
+    std::vector<int> it, st;
+    TRY(cg_run<float>(c, c->x32, c->r32, c->p32, c->Ap32, itol2, c->opt.cg_maxit, it, st));
+    TRY(put_small(c, s, 2 * P, nrm));
+    nfs::k_axpy_promote<<<nb, 256, 0, s>>>(x, c->d_small + 2 * P, c->x32, c->N, tot);
+    CK(cudaGetLastError());
+    // refinement residual with the complex128 product, skipping finished problems
+    TRY(put_flags(c, s, P, skip));
+    TRY(matvec<double>(c, s, x, c->Ap64, c->d_flags + P, 1));
+    TRY(sub64(c, s, b, c->Ap64, c->r64));
+    for (int q = 0; q < P; ++q) {
+      if (skip[q]) continue;
+      so.iters[q] += it[q];
+      so.refines[q] += 1;
+      if (st[q] == NFS_EBREAKDOWN) { so.status[q] = NFS_EBREAKDOWN; live[q] = 0; }
+    }
+  }
+  return NFS_OK;
+}
+
+// --- Lanczos helpers -------------------------------------------------------
+
+// Lanczos scratch layout in dscratch (doubles), mcap the basis capacity:
+//   [0, P * kRedBlocks * 2 * mcap)   per-block partial dots
+//   then P * 2 * mcap                finished dots
+//   then P * 2 * mcap                coefficients for the update
+size_t lanczos_scratch_len(int P, int mcap) {
+  return (size_t)P * kRedBlocks * 2 * mcap + 4 * (size_t)P * mcap + 64;
+}
+size_t off_fin(const nfs_ctx* c) { return (size_t)c->P * kRedBlocks * 2 * c->vcap; }
+size_t off_coef(const nfs_ctx* c) { return off_fin(c) + (size_t)2 * c->P * c->vcap; }
+
+// Per-problem complex inner products of w_p with basis vectors [j0, j0 + m) of
+// Vbase (V or MV, FP64) -> out[p * 2m + 2i + {0,1}] on the host; problems with
+// a zero flag in d_active are skipped.
+int multi_dot(nfs_ctx* c, const double2* Vbase, int j0, int m, const double2* w, std::vector<double>& out,
+              const int* d_active) {
+  cudaStream_t s = c->work;
+  const long long vstride = (long long)c->vcap * c->N;
+  double* part = c->dscratch;
+  double* fin = c->dscratch + off_fin(c);
+  nfs::k_multi_dot<kRedThreads><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(Vbase + (long long)j0 * c->N, vstride,
+                                                                              m, w, c->N, part, d_active);
+  nfs::k_multi_dot_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out.assign(c->hscratch, c->hscratch + (size_t)c->P * 2 * m);
+  return NFS_OK;
+}
+
+// w_p -= V_p[j0 : j0 + m] coef_p ; Mw_p -= MV_p[j0 : j0 + m] coef_p
+int multi_axpy(nfs_ctx* c, double2* w, double2* Mw, int j0, int m, const std::vector<double>& coef,
+               const int* d_active) {
+  cudaStream_t s = c->work;
+  const long long vstride = (long long)c->vcap * c->N;
+  double* dcoef = c->dscratch + off_coef(c);
+  std::memcpy(c->hscratch, coef.data(), coef.size() * sizeof(double));
+  CK(cudaMemcpyAsync(dcoef, c->hscratch, coef.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  nfs::k_multi_axpy<<<dim3(grid_blocks(c->N, 256), c->P), 256, 0, s>>>(
+      w, Mw, c->V + (long long)j0 * c->N, c->MV + (long long)j0 * c->N, vstride, dcoef, m, c->N, d_active);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));  // the pinned staging buffer is reused next
+  return NFS_OK;
+}
+
+// d_p = MV32_p[0:m]^* w_p with the complex64 shadows (orthogonality monitor)
+int shadow_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, const int* d_active) {
+  cudaStream_t s = c->work;
+  const long long vstride = (long long)c->vcap * c->N;
+  nfs::k_to_c64<<<grid_blocks(c->P * c->N, 256), 256, 0, s>>>(w, c->N, c->w32, c->N, c->N, c->P);
+  constexpr int G = 8;
+  double* part = c->dscratch;
+  double* fin = c->dscratch + off_fin(c);
+  nfs::k_shadow_dots<G><<<dim3(kRedBlocks, (m + G - 1) / G, c->P), kRedThreads, 0, s>>>(c->MV32, vstride, m, c->w32,
+                                                                                        c->N, part, d_active);
+  nfs::k_dots_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  out.assign(c->hscratch, c->hscratch + (size_t)c->P * 2 * m);
+  return NFS_OK;
+}
+
+int refresh_shadows(nfs_ctx* c, int first, int count) {
+  const long long vstride = (long long)c->vcap * c->N;
+  const long long len = (long long)count * c->N;
+  const long long off = (long long)first * c->N;
+  const int nb = grid_blocks(len * c->P, 256);
+  nfs::k_to_c64<<<nb, 256, 0, c->work>>>(c->V + off, vstride, c->V32 + off, vstride, len, c->P);
+  nfs::k_to_c64<<<nb, 256, 0, c->work>>>(c->MV + off, vstride, c->MV32 + off, vstride, len, c->P);
+  CK(cudaGetLastError());
   return NFS_OK;
 }
 
 int ensure_basis(nfs_ctx* c, int m) {
   if (c->vcap >= m + 1) return NFS_OK;
-  if (c->V) { cudaFree(c->V); c->bytes -= (long long)c->vcap * c->N * 16; c->V = nullptr; }
-  if (c->MV) { cudaFree(c->MV); c->bytes -= (long long)c->vcap * c->N * 16; c->MV = nullptr; }
+  void* olds[] = {c->V, c->MV, c->V32, c->MV32, c->w32};
+  for (void* p : olds)
+    if (p) cudaFree(p);
+  c->bytes -= (long long)c->P * c->vcap * c->N * (16 + 16 + 8 + 8) + (c->w32 ? c->P * c->N * 8 : 0);
+  c->V = c->MV = nullptr;
+  c->V32 = c->MV32 = c->w32 = nullptr;
   c->vcap = 0;
-  TRY(dalloc(c, &c->V, (size_t)(m + 1) * c->N));
-  TRY(dalloc(c, &c->MV, (size_t)(m + 1) * c->N));
+  const size_t len = (size_t)c->P * (m + 1) * c->N;
+  TRY(dalloc(c, &c->V, len));
+  TRY(dalloc(c, &c->MV, len));
+  TRY(dalloc(c, &c->V32, len));
+  TRY(dalloc(c, &c->MV32, len));
+  TRY(dalloc(c, &c->w32, (size_t)c->P * c->N));
   c->vcap = m + 1;
   return NFS_OK;
 }
 
-// V[0:k] = V[0:m] Y (Y real m x k column-major)
-int rotate(nfs_ctx* c, double2* V, int m, const std::vector<double>& Ycm, int k) {
-  if (c->dY_len < m * k) {
+// V_p[0:k] = V_p[0:m] Y_p for every problem flagged in d_active (Y: P blocks
+// of m x k, column-major); base is V or MV.
+int rotate(nfs_ctx* c, double2* base, int m, const std::vector<double>& Y, int k, const int* d_active) {
+  const size_t need = (size_t)c->P * m * k;
+  if (c->dY_len < need) {
     if (c->dY) cudaFree(c->dY);
     c->dY = nullptr;
-    TRY(dalloc(c, &c->dY, (size_t)m * k));
-    c->dY_len = m * k;
+    TRY(dalloc(c, &c->dY, need));
+    c->dY_len = need;
   }
-  CK(cudaMemcpyAsync(c->dY, Ycm.data(), (size_t)m * k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->dY, Y.data(), need * sizeof(double), cudaMemcpyHostToDevice, c->work));
   constexpr int TE = 32;
   const size_t smem = (size_t)m * TE * sizeof(double2);
   CK(cudaFuncSetAttribute(nfs::k_rotate_basis<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  nfs::k_rotate_basis<TE><<<grid_blocks((c->N + TE - 1) / TE, 1), 256, smem, c->stream>>>(V, m, c->dY, k, c->N);
+  nfs::k_rotate_basis<TE><<<dim3(grid_blocks((c->N + TE - 1) / TE, 1), c->P), 256, smem, c->work>>>(
+      base, (long long)c->vcap * c->N, m, c->dY, k, c->N, d_active);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->work));  // Y's host buffer may be released next
+  return NFS_OK;
+}
+
+// B_r applied to basis vector j of every problem -> out (P x N); t64 is used
+// to gather the vectors contiguously
+int apply_Br_basis(nfs_ctx* c, int j, double2* out) {
+  const long long vstride = (long long)c->vcap * c->N;
+  for (int p = 0; p < c->P; ++p)
+    CK(cudaMemcpyAsync(c->t64 + (long long)p * c->N, c->V + p * vstride + (long long)j * c->N,
+                       c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->work));
+  nfs::k_apply_Br<<<grid_blocks(c->n * c->P, 256), 256, 0, c->work>>>(c->t64, out, c->lam64, c->n1, c->n2, c->n3,
+                                                                      c->P);
   CK(cudaGetLastError());
   return NFS_OK;
 }
 
-int apply_Br(nfs_ctx* c, const double2* v, double2* out) {
-  nfs::k_apply_Br<<<grid_blocks(c->n, 256), 256, 0, c->stream>>>(v, out, c->lam64, c->n1, c->n2, c->n3);
+// Default basis size: generous (device memory is plentiful and restarts cost
+// FP64 basis rotations), capped by half of the free device memory.
+int default_ncv(nfs_ctx* c, int nev) {
+  int m = std::max(std::max(3 * nev, 2 * nev + 2), std::min(8 * nev, 240));
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+    const double per = (double)c->P * c->N * (16 + 16 + 8 + 8);
+    const int cap = (int)std::max(0.0, 0.5 * (double)fr / per) - 1;
+    if (cap < m) m = std::max(cap, 2 * nev + 2);
+  }
+  return m;
+}
+
+// Thick-restart invert Lanczos on (B_r, A_r) for every problem of the
+// context, in lock-step, on the work stream.  omega: host P x nev; Y: device
+// P x nev x N or null; infos: P entries or null.  Returns the worst status.
+int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* infos) {
+  const int P = c->P;
+  const long long N = c->N;
+  int m = c->opt.ncv > 0 ? c->opt.ncv : default_ncv(c, nev);
+  m = (int)std::min<long long>(m, N - 1);
+  if (m <= nev + 1) return NFS_EINVAL;
+  TRY(ensure_basis(c, m));
+  TRY(ensure_scratch(c, lanczos_scratch_len(P, c->vcap)));
+  const long long vstride = (long long)c->vcap * N;
+  cudaStream_t s = c->work;
+  const long long mv32_0 = c->mv32, mv64_0 = c->mv64;
+  const int nb = grid_blocks(P * N, 256);
+  auto col = [&](double2* base, int p, int j) { return base + p * vstride + (long long)j * N; };
+
+  // starting vectors, A_r-normalised (vector 0 of every basis)
+  nfs::k_random_fill<<<nb, 256, 0, s>>>(c->V, N, vstride, P, c->opt.seed);
   CK(cudaGetLastError());
+  for (int p = 0; p < P; ++p)
+    CK(cudaMemcpyAsync(c->t64 + p * N, col(c->V, p, 0), N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  TRY(matvec<double>(c, s, c->t64, c->t64b));
+  std::vector<double> nrm2;
+  TRY(dots_re(c, s, c->t64, c->t64b, nrm2));
+  std::vector<double> sc(P);
+  for (int p = 0; p < P; ++p) {
+    if (!(nrm2[p] > 0)) return NFS_EBREAKDOWN;
+    sc[p] = 1.0 / std::sqrt(nrm2[p]);
+  }
+  TRY(put_small(c, s, P, sc));
+  nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(c->t64, c->t64b, c->d_small + P, c->V, c->MV, c->V32, c->MV32, vstride,
+                                               0, N, P, nullptr);
+  CK(cudaGetLastError());
+
+  const int keep = std::min(m - 1, std::max(nev + 1, nev + (m - nev) / 2));
+  const int check_every = 10;
+  std::vector<std::vector<double>> H(P, std::vector<double>((size_t)m * m, 0.0));
+  std::vector<double> beta_last(P, 0.0);
+  std::vector<int> active(P, 1), jm(P, 0), nconv(P, 0), steps(P, 0), restarts_p(P, 0), force(P, 0);
+  std::vector<long long> cg_total(P, 0);
+  std::vector<int> status(P, NFS_OK);
+  int jstart = 0, local_lo = 0, restarts = 0;
+  std::vector<double> theta, Z, coef, coef2, d, bb;
+  double2* w = c->x64;    // new Krylov vectors (P x N)
+  double2* Mw = c->t64b;  // A_r w
+  int* d_active = c->d_flags;
+  auto leading = [&](int p, int k) {
+    std::vector<double> A((size_t)k * k);
+    for (int r = 0; r < k; ++r)
+      for (int q = 0; q < k; ++q) A[(size_t)r * k + q] = H[p][(size_t)r * m + q];
+    return A;
+  };
+  auto any_active = [&]() {
+    for (int p = 0; p < P; ++p)
+      if (active[p]) return true;
+    return false;
+  };
+  TRY(put_flags(c, s, 0, active));
+  while (any_active()) {
+    for (int j = jstart; j < m && any_active(); ++j) {
+      // w = A_r^{-1} B_r v_j (CG); A_r w = B_r v_j
+      TRY(apply_Br_basis(c, j, Mw));
+      SolveOut so;
+      TRY(solve(c, Mw, w, true, active, so));
+      for (int p = 0; p < P; ++p) {
+        if (!active[p]) continue;
+        if (so.status[p] == NFS_EBREAKDOWN) return NFS_EBREAKDOWN;
+        cg_total[p] += so.iters[p];
+        ++steps[p];
+      }
+      // FP64 three-term recurrence (after a restart: the arrow of kept Ritz
+      // vectors) in the A_r inner product
+      const int nl = j - local_lo + 1;
+      TRY(multi_dot(c, c->MV, local_lo, nl, w, coef, d_active));
+      TRY(multi_axpy(c, w, Mw, local_lo, nl, coef, d_active));
+      std::vector<double> alpha(P);
+      for (int p = 0; p < P; ++p) alpha[p] = coef[(size_t)p * 2 * nl + 2 * (j - local_lo)];
+      TRY(dots_re(c, s, w, Mw, bb));
+      // Partial re-orthogonalisation: measure the loss of orthogonality
+      // against the older vectors with the complex64 shadows (cheap), and
+      // re-orthogonalise exactly in FP64 against the whole basis when it
+      // exceeds the semi-orthogonality level, here and on the next step.
+      std::vector<int> reorth(P, 0);
+      if (local_lo > 0) {
+        TRY(shadow_dots(c, local_lo, w, d, d_active));
+        for (int p = 0; p < P; ++p) {
+          if (!active[p]) continue;
+          if (force[p]) {
+            reorth[p] = 1;
+            force[p] = 0;
+            continue;
+          }
+          double loss = 0.0;
+          for (int i = 0; i < local_lo; ++i)
+            loss = std::max(loss, std::hypot(d[(size_t)p * 2 * local_lo + 2 * i], d[(size_t)p * 2 * local_lo + 2 * i + 1]));
+          loss /= std::sqrt(std::max(bb[p], 1e-300));
+          reorth[p] = loss > kSemiOrthogonality;
+          force[p] = reorth[p];
+        }
+      } else {
+        for (int p = 0; p < P; ++p) {
+          reorth[p] = active[p] && force[p];
+          force[p] = 0;
+        }
+      }
+      bool any_re = false;
+      for (int p = 0; p < P; ++p) {
+        reorth[p] = reorth[p] && active[p];
+        any_re = any_re || reorth[p];
+      }
+      if (any_re) {
+        TRY(put_flags(c, s, P, reorth));
+        for (int pass = 0; pass < 2; ++pass) {
+          TRY(multi_dot(c, c->MV, 0, j + 1, w, coef2, c->d_flags + P));
+          TRY(multi_axpy(c, w, Mw, 0, j + 1, coef2, c->d_flags + P));
+          for (int p = 0; p < P; ++p)
+            if (reorth[p]) alpha[p] += coef2[(size_t)p * 2 * (j + 1) + 2 * j];
+        }
+        TRY(dots_re(c, s, w, Mw, bb));
+      }
+      for (int p = 0; p < P; ++p) {
+        if (!active[p]) continue;
+        if (!(bb[p] > 0)) return NFS_EBREAKDOWN;
+        const double beta = std::sqrt(bb[p]);
+        H[p][(size_t)j * m + j] = alpha[p];
+        if (j + 1 < m) H[p][(size_t)(j + 1) * m + j] = H[p][(size_t)j * m + j + 1] = beta;
+        beta_last[p] = beta;
+        sc[p] = 1.0 / beta;
+      }
+      TRY(put_small(c, s, P, sc));
+      nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(w, Mw, c->d_small + P, c->V, c->MV, c->V32, c->MV32, vstride,
+                                                   j + 1, N, P, d_active);
+      CK(cudaGetLastError());
+      local_lo = j;
+      // Ritz values of the leading (j+1) x (j+1) block; residual |beta z_last|
+      const int k = j + 1;
+      if (k >= nev + 1 && ((k - jstart) % check_every == 0 || j == m - 1)) {
+        bool changed = false;
+        for (int p = 0; p < P; ++p) {
+          if (!active[p]) continue;
+          std::vector<double> zl;
+          if (!nfs::host::sym_eig(k, leading(p, k), theta, zl, true)) return NFS_EBREAKDOWN;
+          int nc = 0;
+          for (int i = 0; i < nev; ++i) {
+            const int cc = k - 1 - i;  // largest theta first
+            if (std::fabs(beta_last[p] * zl[cc]) <= c->opt.eig_tol * std::fabs(theta[cc])) ++nc;
+          }
+          nconv[p] = nc;
+          if (nc == nev) {
+            jm[p] = k;
+            active[p] = 0;
+            changed = true;
+          }
+        }
+        if (changed) TRY(put_flags(c, s, 0, active));
+      }
+    }
+    if (!any_active()) break;
+    if (restarts >= c->opt.max_restarts) {
+      for (int p = 0; p < P; ++p)
+        if (active[p]) {
+          status[p] = NFS_ENOCONV;
+          jm[p] = m;
+          active[p] = 0;
+        }
+      break;
+    }
+    // thick restart of every unconverged problem: keep the `keep` largest
+    // Ritz pairs of its full basis
+    std::vector<double> Ycm((size_t)P * m * keep, 0.0);
+    std::vector<std::vector<double>> th(P), zz(P);
+    for (int p = 0; p < P; ++p) {
+      if (!active[p]) continue;
+      if (!nfs::host::sym_eig(m, leading(p, m), th[p], zz[p])) return NFS_EBREAKDOWN;
+      for (int i = 0; i < keep; ++i)
+        for (int r = 0; r < m; ++r) Ycm[(size_t)p * m * keep + (size_t)i * m + r] = zz[p][(size_t)r * m + (m - 1 - i)];
+    }
+    TRY(rotate(c, c->V, m, Ycm, keep, d_active));
+    TRY(rotate(c, c->MV, m, Ycm, keep, d_active));
+    for (int p = 0; p < P; ++p) {
+      if (!active[p]) continue;
+      CK(cudaMemcpyAsync(col(c->V, p, keep), col(c->V, p, m), N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(col(c->MV, p, keep), col(c->MV, p, m), N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+      std::fill(H[p].begin(), H[p].end(), 0.0);
+      for (int i = 0; i < keep; ++i) {
+        H[p][(size_t)i * m + i] = th[p][m - 1 - i];
+        const double sres = beta_last[p] * zz[p][(size_t)(m - 1) * m + (m - 1 - i)];
+        H[p][(size_t)keep * m + i] = H[p][(size_t)i * m + keep] = sres;
+      }
+      force[p] = 1;  // the first step after a restart couples to every kept vector
+      ++restarts_p[p];
+    }
+    TRY(refresh_shadows(c, 0, keep + 1));
+    jstart = keep;
+    local_lo = 0;
+    ++restarts;
+  }
+  // results from each problem's leading jm x jm block: omega ascending = theta descending
+  int worst = NFS_OK;
+  std::vector<int> one(P, 0);
+  for (int p = 0; p < P; ++p) {
+    const int k = jm[p];
+    if (!nfs::host::sym_eig(k, leading(p, k), theta, Z)) return NFS_EBREAKDOWN;
+    double maxres = 0.0;
+    for (int i = 0; i < nev; ++i) {
+      const int cc = k - 1 - i;
+      omega[(size_t)p * nev + i] = 1.0 / theta[cc];
+      maxres = std::max(maxres, std::fabs(beta_last[p] * Z[(size_t)(k - 1) * k + cc]) / std::fabs(theta[cc]));
+    }
+    if (Y) {
+      // Ritz vectors of problem p: rotate its basis (only p flagged), then copy
+      std::vector<double> Ycm((size_t)P * k * nev, 0.0);
+      for (int i = 0; i < nev; ++i)
+        for (int r = 0; r < k; ++r) Ycm[(size_t)p * k * nev + (size_t)i * k + r] = Z[(size_t)r * k + (k - 1 - i)];
+      std::fill(one.begin(), one.end(), 0);
+      one[p] = 1;
+      TRY(put_flags(c, s, P, one));
+      TRY(rotate(c, c->V, k, Ycm, nev, c->d_flags + P));
+      CK(cudaMemcpyAsync(Y + (long long)p * nev * N, col(c->V, p, 0), (size_t)nev * N * sizeof(double2),
+                         cudaMemcpyDeviceToDevice, s));
+    }
+    if (infos) {
+      nfs_eigs_info& in = infos[p];
+      in.lanczos_steps = steps[p];
+      in.restarts = restarts_p[p];
+      in.cg_iterations = cg_total[p];
+      in.matvecs_c64 = (c->mv32 - mv32_0) / P;
+      in.matvecs_c128 = (c->mv64 - mv64_0) / P;
+      in.nconv = status[p] == NFS_OK ? nev : nconv[p];
+      in.max_ritz_residual = maxres;
+      in.status = status[p];
+    }
+    if (status[p] != NFS_OK) worst = status[p];
+  }
+  CK(cudaStreamSynchronize(s));
+  return worst;
+}
+
+// Order the context's work stream after everything already queued on the
+// caller's stream.
+int join_caller(nfs_ctx* c) {
+  CK(cudaEventRecord(c->ev, c->stream));
+  CK(cudaStreamWaitEvent(c->work, c->ev, 0));
   return NFS_OK;
 }
 
 void free_ctx(nfs_ctx* c) {
   if (!c) return;
+  for (GraphEntry& g : c->graphs) cudaGraphExecDestroy(g.exec);
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
                   c->mat64, c->mat32, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
-                  c->p32, c->Ap32, c->st, c->dscratch, c->V, c->MV, c->dY};
+                  c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
+                  c->w32, c->dY};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
   if (c->hscratch) cudaFreeHost(c->hscratch);
+  if (c->work) cudaStreamDestroy(c->work);
+  if (c->ev) cudaEventDestroy(c->ev);
   delete c;
+}
+
+// --- set-up -------------------------------------------------------------------
+
+struct Prepared {
+  double kd[3];
+  std::vector<double2> lam;
+  std::vector<double> m64;
+};
+
+int check_options(const nfs_options& o) {
+  if (o.precision != NFS_PREC_FP64 && o.precision != NFS_PREC_MIXED) return NFS_EINVAL;
+  if (!(o.cg_tol > 0) || o.cg_maxit <= 0 || !(o.eig_tol > 0) || o.max_restarts < 0) return NFS_EINVAL;
+  if (o.precision == NFS_PREC_MIXED && (!(o.inner_tol > 0) || o.inner_tol >= 1 || o.max_refine <= 0))
+    return NFS_EINVAL;
+  if (!(o.alpha != 0.0) || !(o.beta != 0.0)) return NFS_EBASIS;
+  return NFS_OK;
+}
+
+// Validate one problem and build its tables and material (host, FP64): the
+// Lemma (lem:nonsingular_full_rank) and the Assumption (eq. assump).
+int prepare_problem(const int grid[3], const double* lattice, const double k[3], const nfs_material* mat,
+                    const nfs_options& o, Prepared& out, double delta[3]) {
+  if (!grid || !k || !mat || !mat->eps || !mat->gamma) return NFS_EINVAL;
+  for (int l = 0; l < 3; ++l)
+    if (grid[l] <= 0) return NFS_EINVAL;
+  if (mat->kind != NFS_MEDIUM_CHIRAL && mat->kind != NFS_MEDIUM_PSEUDOCHIRAL) return NFS_EINVAL;
+  if (mat->kind == NFS_MEDIUM_PSEUDOCHIRAL &&
+      (mat->axis_a < 0 || mat->axis_a > 2 || mat->axis_b < 0 || mat->axis_b > 2 || mat->axis_a == mat->axis_b))
+    return NFS_EINVAL;
+  const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
+  if (!size_ok(n1) || !size_ok(n2) || !size_ok(n3) || n1 != n2) return NFS_EUNSUPPORTED;
+  if (!nfs::matvec_supported<double>(n1, n2, n3) || !nfs::matvec_supported<float>(n1, n2, n3))
+    return NFS_EUNSUPPORTED;
+  double a_len[3] = {1.0, 1.0, 1.0};
+  if (lattice) {
+    for (int r = 0; r < 3; ++r)
+      for (int s = 0; s < 3; ++s)
+        if (r != s && lattice[3 * r + s] != 0.0) return NFS_EUNSUPPORTED;
+    for (int l = 0; l < 3; ++l) {
+      a_len[l] = std::fabs(lattice[4 * l]);
+      if (!(a_len[l] > 0)) return NFS_EINVAL;
+    }
+  }
+  const long long n = (long long)n1 * n2 * n3;
+  const int nn[3] = {n1, n2, n3};
+  bool all_int = true;
+  for (int l = 0; l < 3; ++l) {
+    if (!std::isfinite(k[l])) return NFS_EINVAL;
+    out.kd[l] = k[l] * a_len[l];
+    delta[l] = a_len[l] / nn[l];
+    if (std::fabs(out.kd[l] - std::round(out.kd[l])) > 1e-12) all_int = false;
+  }
+  if (all_int) return NFS_EKPOINT;
+
+  // Lambda tables (thm:SchurDecomp_Ci): (exp(i 2 pi (i + k.a)/m) - 1) / delta,
+  // real part written as -2 sin^2(theta/2) to avoid cancellation.
+  out.lam.assign(n1 + n2 + n3, make_double2(0, 0));
+  {
+    int off = 0;
+    for (int l = 0; l < 3; ++l) {
+      for (int i = 0; i < nn[l]; ++i) {
+        const double th = 2.0 * M_PI * (i + out.kd[l]) / nn[l];
+        const double sh = std::sin(0.5 * th);
+        out.lam[off + i] = make_double2(-2.0 * sh * sh / delta[l], std::sin(th) / delta[l]);
+      }
+      off += nn[l];
+    }
+  }
+  // Lemma: Lambda_q > 0 and Lambda_p != 0 at every voxel
+  {
+    const double al = o.alpha, be = o.beta;
+    double minq = INFINITY, minp = INFINITY;
+    for (int i3 = 0; i3 < n3; ++i3)
+      for (int i2 = 0; i2 < n2; ++i2)
+        for (int i1 = 0; i1 < n1; ++i1) {
+          const double2 a1 = out.lam[i1], a2 = out.lam[n1 + i2], a3 = out.lam[n1 + n2 + i3];
+          const double lq = nfs::cabs2(a1) + nfs::cabs2(a2) + nfs::cabs2(a3);
+          const double2 p1 = make_double2(be * a3.x - a2.x, be * a3.y - a2.y);
+          const double2 p2 = make_double2(a1.x - al * a3.x, a1.y - al * a3.y);
+          const double2 p3 = make_double2(al * a2.x - be * a1.x, al * a2.y - be * a1.y);
+          const double lp = nfs::cabs2(p1) + nfs::cabs2(p2) + nfs::cabs2(p3);
+          minq = std::min(minq, lq);
+          minp = std::min(minp, lp / ((al * al + be * be + 1.0) * lq));
+        }
+    if (!(minq > 0)) return NFS_EKPOINT;
+    if (!(minp > 1e-13)) return NFS_EBASIS;
+  }
+  // material (Section 4.3): 1/Phi, gamma, 1/mu per component; Assumption check
+  const bool has_mu = mat->mu != nullptr;
+  const long long gam_len = (mat->kind == NFS_MEDIUM_CHIRAL) ? 3 * n : n;
+  const long long mat_len = 3 * n + gam_len + (has_mu ? 3 * n : 0);
+  out.m64.assign(mat_len, 0.0);
+  double* inv_phi = out.m64.data();
+  double* gam = inv_phi + 3 * n;
+  double* inv_mu = gam + gam_len;
+  for (long long i = 0; i < gam_len; ++i) {
+    if (!std::isfinite(mat->gamma[i])) return NFS_EINVAL;
+    gam[i] = mat->gamma[i];
+  }
+  for (long long i = 0; i < 3 * n; ++i) {
+    const double mu = has_mu ? mat->mu[i] : 1.0;
+    if (!(mu > 0) || !std::isfinite(mu) || !std::isfinite(mat->eps[i])) return NFS_ENOTHPD;
+    if (has_mu) inv_mu[i] = 1.0 / mu;
+  }
+  for (int cpt = 0; cpt < 3; ++cpt) {
+    for (long long v = 0; v < n; ++v) {
+      const long long i = cpt * n + v;
+      double phi;
+      if (mat->kind == NFS_MEDIUM_CHIRAL) {
+        const double mu = has_mu ? mat->mu[i] : 1.0;
+        phi = mat->eps[i] - gam[i] * gam[i] / mu;
+      } else {
+        const int a = mat->axis_a, b = mat->axis_b;
+        const double g = gam[v];
+        if (cpt == a) phi = mat->eps[i] - g * g / (has_mu ? mat->mu[b * n + v] : 1.0);
+        else if (cpt == b) phi = mat->eps[i] - g * g / (has_mu ? mat->mu[a * n + v] : 1.0);
+        else phi = mat->eps[i];
+      }
+      if (!(phi > 0)) return NFS_ENOTHPD;
+      inv_phi[i] = 1.0 / phi;
+    }
+  }
+  return NFS_OK;
+}
+
+// Host-side validation and tables for P problems that share grid, medium
+// kind, axis pair and mu-ness (no CUDA call).
+int prepare_class(int P, const int grid[3], const double* const* lattices, const double* const* ks,
+                  const nfs_material* const* mats, const nfs_options& o, std::vector<Prepared>& prep,
+                  double delta[3]) {
+  prep.assign(P, Prepared{});
+  for (int p = 0; p < P; ++p) TRY(prepare_problem(grid, lattices[p], ks[p], mats[p], o, prep[p], delta));
+  const nfs_material* m0 = mats[0];
+  for (int p = 1; p < P; ++p) {
+    if (mats[p]->kind != m0->kind || (mats[p]->mu != nullptr) != (m0->mu != nullptr)) return NFS_EINVAL;
+    if (m0->kind == NFS_MEDIUM_PSEUDOCHIRAL && (mats[p]->axis_a != m0->axis_a || mats[p]->axis_b != m0->axis_b))
+      return NFS_EINVAL;
+  }
+  return NFS_OK;
+}
+
+// The device side of a context for a prepared class.
+int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* const* mats,
+                const std::vector<Prepared>& prep, const double delta[3], const nfs_options& o) {
+  *out = nullptr;
+  const nfs_material* m0 = mats[0];
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  nfs_ctx* c = new (std::nothrow) nfs_ctx();
+  if (!c) return NFS_ENOMEM;
+  const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
+  c->n1 = n1; c->n2 = n2; c->n3 = n3; c->nl = n1 + n2 + n3;
+  c->n = (long long)n1 * n2 * n3;
+  c->N = 4 * c->n;
+  c->P = P;
+  for (int l = 0; l < 3; ++l) c->delta[l] = delta[l];
+  c->opt = o;
+  c->stream = (cudaStream_t)o.stream;
+  c->kind = m0->kind;
+  c->ax_a = c->kind == NFS_MEDIUM_CHIRAL ? 0 : m0->axis_a;
+  c->ax_b = c->kind == NFS_MEDIUM_CHIRAL ? 1 : m0->axis_b;
+  c->has_mu = m0->mu != nullptr;
+  c->gam_len = (c->kind == NFS_MEDIUM_CHIRAL) ? 3 * c->n : c->n;
+  c->mat_len = (long long)prep[0].m64.size();
+
+  auto fail = [&](int code) { free_ctx(c); return code; };
+#define TRYC(call)                         \
+  do {                                     \
+    int r_ = (call);                       \
+    if (r_ != NFS_OK) return fail(r_);     \
+  } while (0)
+#define CKC(call)                                               \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call));   \
+  } while (0)
+
+  CKC(cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+  const int nl = c->nl;
+  {
+    std::vector<double2> lam((size_t)P * nl);
+    std::vector<float2> lam32((size_t)P * nl);
+    for (int p = 0; p < P; ++p)
+      for (int i = 0; i < nl; ++i) {
+        lam[(size_t)p * nl + i] = prep[p].lam[i];
+        lam32[(size_t)p * nl + i] = make_float2((float)prep[p].lam[i].x, (float)prep[p].lam[i].y);
+      }
+    TRYC(dalloc(c, &c->lam64, (size_t)P * nl));
+    TRYC(dalloc(c, &c->lam32, (size_t)P * nl));
+    CKC(cudaMemcpy(c->lam64, lam.data(), lam.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(c->lam32, lam32.data(), lam32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
+  const int nn[3] = {n1, n2, n3};
+  for (int l = 0; l < 3; ++l) {
+    const int m = nn[l];
+    std::vector<double2> t(m);
+    std::vector<float2> t32(m);
+    for (int i = 0; i < m; ++i) {
+      const double th = -2.0 * M_PI * i / m;
+      t[i] = make_double2(std::cos(th), std::sin(th));
+      t32[i] = make_float2((float)t[i].x, (float)t[i].y);
+    }
+    TRYC(dalloc(c, &c->tw64[l], m));
+    TRYC(dalloc(c, &c->tw32[l], m));
+    CKC(cudaMemcpy(c->tw64[l], t.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
+    CKC(cudaMemcpy(c->tw32[l], t32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
+  }
+  {
+    const size_t ml = (size_t)c->mat_len;
+    TRYC(dalloc(c, &c->mat64, (size_t)P * ml));
+    TRYC(dalloc(c, &c->mat32, (size_t)P * ml));
+    std::vector<float> m32(ml);
+    for (int p = 0; p < P; ++p) {
+      for (size_t i = 0; i < ml; ++i) m32[i] = (float)prep[p].m64[i];
+      CKC(cudaMemcpy(c->mat64 + (size_t)p * ml, prep[p].m64.data(), ml * sizeof(double), cudaMemcpyHostToDevice));
+      CKC(cudaMemcpy(c->mat32 + (size_t)p * ml, m32.data(), ml * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+  const size_t PN = (size_t)P * c->N;
+  TRYC(dalloc(c, (double2**)&c->fld, (size_t)P * 6 * c->n));
+  TRYC(dalloc(c, &c->x64, PN));
+  TRYC(dalloc(c, &c->r64, PN));
+  TRYC(dalloc(c, &c->p64, PN));
+  TRYC(dalloc(c, &c->Ap64, PN));
+  TRYC(dalloc(c, &c->t64, PN));
+  TRYC(dalloc(c, &c->t64b, PN));
+  if (o.precision == NFS_PREC_MIXED) {
+    TRYC(dalloc(c, &c->x32, PN));
+    TRYC(dalloc(c, &c->r32, PN));
+    TRYC(dalloc(c, &c->p32, PN));
+    TRYC(dalloc(c, &c->Ap32, PN));
+  }
+  TRYC(dalloc(c, &c->st, P));
+  CKC(cudaMallocHost((void**)&c->st_host, (size_t)P * sizeof(CGState)));
+  std::memset(c->st_host, 0, (size_t)P * sizeof(CGState));
+  CKC(cudaMemset(c->st, 0, (size_t)P * sizeof(CGState)));
+  TRYC(dalloc(c, &c->d_small, (size_t)kSmallSlots * P));
+  CKC(cudaMallocHost((void**)&c->h_small, (size_t)kSmallSlots * P * sizeof(double)));
+  TRYC(dalloc(c, &c->d_flags, (size_t)kFlagSlots * P));
+  CKC(cudaMallocHost((void**)&c->h_flags, (size_t)kFlagSlots * P * sizeof(int)));
+  TRYC(ensure_scratch(c, (size_t)kRedBlocks * 2 * 64 * P + 4096));
+  CKC(nfs::matvec_prepare<double>(n1, n2, n3));
+  CKC(nfs::matvec_prepare<float>(n1, n2, n3));
+  CKC(nfs::grad_prepare(n1, n2, n3));
+  CKC(cudaDeviceSynchronize());
+#undef TRYC
+#undef CKC
+  *out = c;
+  return NFS_OK;
+}
+
+nfs_options resolved_options(const nfs_options* opt) {
+  nfs_options o;
+  nfs_default_options(&o);
+  if (opt) o = *opt;
+  return o;
 }
 
 }  // namespace
@@ -470,206 +1155,22 @@ extern "C" int nfs_setup(nfs_ctx** out, const int grid[3], const double* lattice
                          const nfs_material* mat, const nfs_options* opt) {
   if (!out) return NFS_EINVAL;
   *out = nullptr;
-  if (!grid || !k || !mat || !mat->eps || !mat->gamma) return NFS_EINVAL;
-  for (int l = 0; l < 3; ++l)
-    if (grid[l] <= 0) return NFS_EINVAL;
-  if (mat->kind != NFS_MEDIUM_CHIRAL && mat->kind != NFS_MEDIUM_PSEUDOCHIRAL) return NFS_EINVAL;
-  if (mat->kind == NFS_MEDIUM_PSEUDOCHIRAL &&
-      (mat->axis_a < 0 || mat->axis_a > 2 || mat->axis_b < 0 || mat->axis_b > 2 || mat->axis_a == mat->axis_b))
-    return NFS_EINVAL;
-  nfs_options o;
-  nfs_default_options(&o);
-  if (opt) o = *opt;
-  if (o.precision != NFS_PREC_FP64 && o.precision != NFS_PREC_MIXED) return NFS_EINVAL;
-  if (!(o.cg_tol > 0) || o.cg_maxit <= 0 || !(o.eig_tol > 0) || o.max_restarts < 0) return NFS_EINVAL;
-  if (o.precision == NFS_PREC_MIXED && (!(o.inner_tol > 0) || o.inner_tol >= 1 || o.max_refine <= 0))
-    return NFS_EINVAL;
-  if (!(o.alpha != 0.0) || !(o.beta != 0.0)) return NFS_EBASIS;
-
-  const int n1 = grid[0], n2 = grid[1], n3 = grid[2];
-  if (!size_ok(n1) || !size_ok(n2) || !size_ok(n3) || n1 != n2) return NFS_EUNSUPPORTED;
-  if (!nfs::matvec_supported<double>(n1, n2, n3) || !nfs::matvec_supported<float>(n1, n2, n3))
-    return NFS_EUNSUPPORTED;
-  double a_len[3] = {1.0, 1.0, 1.0};
-  if (lattice) {
-    for (int r = 0; r < 3; ++r)
-      for (int s = 0; s < 3; ++s)
-        if (r != s && lattice[3 * r + s] != 0.0) return NFS_EUNSUPPORTED;
-    for (int l = 0; l < 3; ++l) {
-      a_len[l] = std::fabs(lattice[4 * l]);
-      if (!(a_len[l] > 0)) return NFS_EINVAL;
-    }
-  }
-  const long long n = (long long)n1 * n2 * n3;
-  double kd[3], delta[3];
-  const int nn[3] = {n1, n2, n3};
-  bool all_int = true;
-  for (int l = 0; l < 3; ++l) {
-    if (!std::isfinite(k[l])) return NFS_EINVAL;
-    kd[l] = k[l] * a_len[l];
-    delta[l] = a_len[l] / nn[l];
-    if (std::fabs(kd[l] - std::round(kd[l])) > 1e-12) all_int = false;
-  }
-  if (all_int) return NFS_EKPOINT;
-
-  // Lambda tables (thm:SchurDecomp_Ci): (exp(i 2 pi (i + k.a)/m) - 1) / delta,
-  // real part written as -2 sin^2(theta/2) to avoid cancellation.
-  std::vector<double2> lam(n1 + n2 + n3);
-  {
-    int off = 0;
-    for (int l = 0; l < 3; ++l) {
-      for (int i = 0; i < nn[l]; ++i) {
-        const double th = 2.0 * M_PI * (i + kd[l]) / nn[l];
-        const double sh = std::sin(0.5 * th);
-        lam[off + i] = make_double2(-2.0 * sh * sh / delta[l], std::sin(th) / delta[l]);
-      }
-      off += nn[l];
-    }
-  }
-  // Lemma (lem:nonsingular_full_rank): Lambda_q > 0 and Lambda_p != 0 at every voxel
-  {
-    const double al = o.alpha, be = o.beta;
-    double minq = INFINITY, minp = INFINITY;
-    for (int i3 = 0; i3 < n3; ++i3)
-      for (int i2 = 0; i2 < n2; ++i2)
-        for (int i1 = 0; i1 < n1; ++i1) {
-          const double2 a1 = lam[i1], a2 = lam[n1 + i2], a3 = lam[n1 + n2 + i3];
-          const double lq = nfs::cabs2(a1) + nfs::cabs2(a2) + nfs::cabs2(a3);
-          const double2 p1 = make_double2(be * a3.x - a2.x, be * a3.y - a2.y);
-          const double2 p2 = make_double2(a1.x - al * a3.x, a1.y - al * a3.y);
-          const double2 p3 = make_double2(al * a2.x - be * a1.x, al * a2.y - be * a1.y);
-          const double lp = nfs::cabs2(p1) + nfs::cabs2(p2) + nfs::cabs2(p3);
-          minq = std::min(minq, lq);
-          minp = std::min(minp, lp / ((al * al + be * be + 1.0) * lq));
-        }
-    if (!(minq > 0)) return NFS_EKPOINT;
-    if (!(minp > 1e-13)) return NFS_EBASIS;
-  }
-
-  // material (Section 4.3): 1/Phi, gamma, 1/mu per component; Assumption check
-  const bool has_mu = mat->mu != nullptr;
-  const long long gam_len = (mat->kind == NFS_MEDIUM_CHIRAL) ? 3 * n : n;
-  const long long mat_len = 3 * n + gam_len + (has_mu ? 3 * n : 0);
-  std::vector<double> m64(mat_len);
-  {
-    double* inv_phi = m64.data();
-    double* gam = inv_phi + 3 * n;
-    double* inv_mu = gam + gam_len;
-    for (long long i = 0; i < gam_len; ++i) {
-      if (!std::isfinite(mat->gamma[i])) return NFS_EINVAL;
-      gam[i] = mat->gamma[i];
-    }
-    for (long long i = 0; i < 3 * n; ++i) {
-      const double mu = has_mu ? mat->mu[i] : 1.0;
-      if (!(mu > 0) || !std::isfinite(mu) || !std::isfinite(mat->eps[i])) return NFS_ENOTHPD;
-      if (has_mu) inv_mu[i] = 1.0 / mu;
-    }
-    for (int cpt = 0; cpt < 3; ++cpt) {
-      for (long long v = 0; v < n; ++v) {
-        const long long i = cpt * n + v;
-        double phi;
-        if (mat->kind == NFS_MEDIUM_CHIRAL) {
-          const double mu = has_mu ? mat->mu[i] : 1.0;
-          phi = mat->eps[i] - gam[i] * gam[i] / mu;
-        } else {
-          const int a = mat->axis_a, b = mat->axis_b;
-          const double g = gam[v];
-          if (cpt == a) phi = mat->eps[i] - g * g / (has_mu ? mat->mu[b * n + v] : 1.0);
-          else if (cpt == b) phi = mat->eps[i] - g * g / (has_mu ? mat->mu[a * n + v] : 1.0);
-          else phi = mat->eps[i];
-        }
-        if (!(phi > 0)) return NFS_ENOTHPD;
-        inv_phi[i] = 1.0 / phi;
-      }
-    }
-  }
-
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
-  nfs_ctx* c = new (std::nothrow) nfs_ctx();
-  if (!c) return NFS_ENOMEM;
-  c->n1 = n1; c->n2 = n2; c->n3 = n3; c->n = n; c->N = 4 * n;
-  for (int l = 0; l < 3; ++l) { c->kdota[l] = kd[l]; c->delta[l] = delta[l]; }
-  c->opt = o;
-  c->stream = (cudaStream_t)o.stream;
-  c->kind = mat->kind; c->ax_a = mat->axis_a; c->ax_b = mat->axis_b;
-  if (c->kind == NFS_MEDIUM_CHIRAL) { c->ax_a = 0; c->ax_b = 1; }
-  c->has_mu = has_mu;
-  c->gam_len = gam_len;
-
-  auto fail = [&](int code) { free_ctx(c); return code; };
-#define TRYC(call)                         \
-  do {                                     \
-    int r_ = (call);                       \
-    if (r_ != NFS_OK) return fail(r_);     \
-  } while (0)
-#define CKC(call)                                               \
-  do {                                                          \
-    cudaError_t e_ = (call);                                    \
-    if (e_ != cudaSuccess) return fail(cuda_fail(e_, #call));   \
-  } while (0)
-
-  const int nl = n1 + n2 + n3;
-  TRYC(dalloc(c, &c->lam64, nl));
-  TRYC(dalloc(c, &c->lam32, nl));
-  std::vector<float2> lam32(nl);
-  for (int i = 0; i < nl; ++i) lam32[i] = make_float2((float)lam[i].x, (float)lam[i].y);
-  CKC(cudaMemcpy(c->lam64, lam.data(), nl * sizeof(double2), cudaMemcpyHostToDevice));
-  CKC(cudaMemcpy(c->lam32, lam32.data(), nl * sizeof(float2), cudaMemcpyHostToDevice));
-  for (int l = 0; l < 3; ++l) {
-    const int m = nn[l];
-    std::vector<double2> t(m);
-    std::vector<float2> t32(m);
-    for (int i = 0; i < m; ++i) {
-      const double th = -2.0 * M_PI * i / m;
-      t[i] = make_double2(std::cos(th), std::sin(th));
-      t32[i] = make_float2((float)t[i].x, (float)t[i].y);
-    }
-    TRYC(dalloc(c, &c->tw64[l], m));
-    TRYC(dalloc(c, &c->tw32[l], m));
-    CKC(cudaMemcpy(c->tw64[l], t.data(), m * sizeof(double2), cudaMemcpyHostToDevice));
-    CKC(cudaMemcpy(c->tw32[l], t32.data(), m * sizeof(float2), cudaMemcpyHostToDevice));
-  }
-  TRYC(dalloc(c, &c->mat64, mat_len));
-  TRYC(dalloc(c, &c->mat32, mat_len));
-  {
-    std::vector<float> m32(mat_len);
-    for (long long i = 0; i < mat_len; ++i) m32[i] = (float)m64[i];
-    CKC(cudaMemcpy(c->mat64, m64.data(), mat_len * sizeof(double), cudaMemcpyHostToDevice));
-    CKC(cudaMemcpy(c->mat32, m32.data(), mat_len * sizeof(float), cudaMemcpyHostToDevice));
-  }
-  const long long N = c->N;
-  TRYC(dalloc(c, (double2**)&c->fld, 6 * n));
-  TRYC(dalloc(c, &c->x64, N));
-  TRYC(dalloc(c, &c->r64, N));
-  TRYC(dalloc(c, &c->p64, N));
-  TRYC(dalloc(c, &c->Ap64, N));
-  TRYC(dalloc(c, &c->t64, N));
-  TRYC(dalloc(c, &c->t64b, N));
-  if (o.precision == NFS_PREC_MIXED) {
-    TRYC(dalloc(c, &c->x32, N));
-    TRYC(dalloc(c, &c->r32, N));
-    TRYC(dalloc(c, &c->p32, N));
-    TRYC(dalloc(c, &c->Ap32, N));
-  }
-  TRYC(dalloc(c, &c->st, 1));
-  CKC(cudaMallocHost((void**)&c->st_host, sizeof(CGState)));
-  std::memset(c->st_host, 0, sizeof(CGState));
-  CKC(cudaMemset(c->st, 0, sizeof(CGState)));
-  TRYC(ensure_scratch(c, (size_t)kRedBlocks * 2 * 64 + 4096));
-  CKC(nfs::matvec_prepare<double>(n1, n2, n3));
-  CKC(nfs::matvec_prepare<float>(n1, n2, n3));
-  CKC(nfs::grad_prepare(n1, n2, n3));
-  CKC(cudaDeviceSynchronize());
-#undef TRYC
-#undef CKC
-  *out = c;
-  return NFS_OK;
+  if (!grid || !k || !mat) return NFS_EINVAL;
+  const nfs_options o = resolved_options(opt);
+  TRY(check_options(o));
+  const double* lat[1] = {lattice};
+  const double* ks[1] = {k};
+  const nfs_material* ms[1] = {mat};
+  std::vector<Prepared> prep;
+  double delta[3] = {0, 0, 0};
+  TRY(prepare_class(1, grid, lat, ks, ms, o, prep, delta));
+  return setup_class(out, 1, grid, ms, prep, delta, o);
 }
 
 extern "C" void nfs_destroy(nfs_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->work);
   free_ctx(c);
 }
 
@@ -685,8 +1186,9 @@ extern "C" int nfs_set_stream(nfs_ctx* c, void* stream) {
 
 extern "C" int nfs_matvec(nfs_ctx* c, int dtype, const void* u, void* Au) {
   if (!c || !u || !Au || u == Au) return NFS_EINVAL;
-  if (dtype == NFS_C128) return matvec<double>(c, (const double2*)u, (double2*)Au);
-  if (dtype == NFS_C64) return matvec<float>(c, (const float2*)u, (float2*)Au);
+  if (((uintptr_t)u | (uintptr_t)Au) & 15) return NFS_EINVAL;  // 16-byte vector access
+  if (dtype == NFS_C128) return matvec<double>(c, c->stream, (const double2*)u, (double2*)Au);
+  if (dtype == NFS_C64) return matvec<float>(c, c->stream, (const float2*)u, (float2*)Au);
   return NFS_EINVAL;
 }
 
@@ -694,6 +1196,7 @@ extern "C" int nfs_matvec_passes(nfs_ctx* c, int dtype, int mask, const void* u,
   if (!c || mask <= 0 || mask > 7) return NFS_EINVAL;
   if ((mask & 1) && !u) return NFS_EINVAL;
   if ((mask & 4) && !Au) return NFS_EINVAL;
+  if (((uintptr_t)u | (uintptr_t)Au) & 15) return NFS_EINVAL;
   cudaError_t e;
   if (dtype == NFS_C128)
     e = nfs::matvec_launch_mask<double>(margs<double>(c, (const double2*)u, (double2*)Au, nullptr), mask);
@@ -707,166 +1210,173 @@ extern "C" int nfs_matvec_passes(nfs_ctx* c, int dtype, int mask, const void* u,
 
 extern "C" int nfs_apply_Br(nfs_ctx* c, const void* v, void* out) {
   if (!c || !v || !out || v == out) return NFS_EINVAL;
-  return apply_Br(c, (const double2*)v, (double2*)out);
+  nfs::k_apply_Br<<<grid_blocks(c->n * c->P, 256), 256, 0, c->stream>>>((const double2*)v, (double2*)out, c->lam64,
+                                                                          c->n1, c->n2, c->n3, c->P);
+  CK(cudaGetLastError());
+  return NFS_OK;
 }
 
 extern "C" int nfs_cg_solve(nfs_ctx* c, const void* b, void* x, nfs_solve_info* info) {
   if (!c || !b || !x || b == x) return NFS_EINVAL;
-  const int r = solve(c, (const double2*)b, (double2*)x, false, info);
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "nfs_cg_solve");
-  return r;
+  if (((uintptr_t)b | (uintptr_t)x) & 15) return NFS_EINVAL;
+  TRY(join_caller(c));
+  // the solve runs on the context's buffers (so that its CUDA graph is reused)
+  const size_t bytes = (size_t)c->P * c->N * sizeof(double2);
+  CK(cudaMemcpyAsync(c->t64b, b, bytes, cudaMemcpyDeviceToDevice, c->work));
+  CK(cudaMemcpyAsync(c->t64, x, bytes, cudaMemcpyDeviceToDevice, c->work));
+  SolveOut so;
+  std::vector<int> active(c->P, 1);
+  TRY(solve(c, c->t64b, c->t64, false, active, so));
+  CK(cudaMemcpyAsync(x, c->t64, bytes, cudaMemcpyDeviceToDevice, c->work));
+  CK(cudaStreamSynchronize(c->work));
+  if (info) {
+    info->iterations = so.iters[0];
+    info->refinements = so.refines[0];
+    info->rel_residual = so.relres[0];
+    info->status = so.status[0];
+  }
+  return so.status[0];
 }
 
 extern "C" int nfs_eigs(nfs_ctx* c, int nev, double* omega, void* Y, nfs_eigs_info* info) {
   if (!c || !omega || nev <= 0 || nev >= c->N / 2) return NFS_EINVAL;
-  const long long N = c->N;
-  int m = c->opt.ncv > 0 ? c->opt.ncv : std::max(3 * nev, 2 * nev + 2);
-  m = (int)std::min<long long>(m, N - 1);
-  if (m <= nev + 1) return NFS_EINVAL;
-  TRY(ensure_basis(c, m));
-  TRY(ensure_scratch(c, lanczos_scratch_len(c->vcap)));
-  const long long mv32_0 = c->mv32, mv64_0 = c->mv64;
-  double2* V = c->V;
-  double2* MV = c->MV;
-  auto vec = [&](double2* base, int j) { return base + (long long)j * N; };
-  const int nb = grid_blocks(N, 256);
-
-  // starting vector, A_r-normalised
-  nfs::k_random_fill<<<nb, 256, 0, c->stream>>>(vec(V, 0), N, c->opt.seed);
-  CK(cudaGetLastError());
-  TRY(matvec<double>(c, vec(V, 0), vec(MV, 0)));
-  double nrm2;
-  TRY(dot_re(c, vec(V, 0), vec(MV, 0), &nrm2));
-  if (!(nrm2 > 0)) return NFS_EBREAKDOWN;
-  nfs::k_scale<double2><<<nb, 256, 0, c->stream>>>(vec(V, 0), 1.0 / std::sqrt(nrm2), N);
-  nfs::k_scale<double2><<<nb, 256, 0, c->stream>>>(vec(MV, 0), 1.0 / std::sqrt(nrm2), N);
-  CK(cudaGetLastError());
-
-  const int keep = std::min(m - 1, std::max(nev + 1, nev + (m - nev) / 2));
-  std::vector<double> H((size_t)m * m, 0.0);
-  int jstart = 0;
-  double beta_last = 0.0;
-  long long cg_total = 0;
-  int steps = 0, restarts = 0, nconv = 0, status = NFS_OK;
-  std::vector<double> theta, Z, coef, coef2;
-  std::vector<int> order;
-  double2* w = c->t64;    // new Krylov vector
-  double2* Mw = c->t64b;  // A_r w
-  for (;;) {
-    for (int j = jstart; j < m; ++j) {
-      // w = A_r^{-1} B_r v_j (CG); A_r w = B_r v_j
-      TRY(apply_Br(c, vec(V, j), Mw));
-      nfs_solve_info si{};
-      const int rs = solve(c, Mw, w, true, &si);
-      if (rs == NFS_EBREAKDOWN) return NFS_EBREAKDOWN;
-      cg_total += si.iterations;
-      ++steps;
-      // classical Gram-Schmidt, twice, in the A_r inner product
-      TRY(multi_dot(c, MV, j + 1, w, coef));
-      TRY(multi_axpy(c, w, Mw, V, MV, j + 1, coef));
-      TRY(multi_dot(c, MV, j + 1, w, coef2));
-      TRY(multi_axpy(c, w, Mw, V, MV, j + 1, coef2));
-      const double alpha = coef[2 * j] + coef2[2 * j];
-      double bb;
-      TRY(dot_re(c, w, Mw, &bb));
-      if (!(bb > 0)) return NFS_EBREAKDOWN;
-      const double beta = std::sqrt(bb);
-      H[(size_t)j * m + j] = alpha;
-      if (j + 1 < m) H[(size_t)(j + 1) * m + j] = H[(size_t)j * m + j + 1] = beta;
-      beta_last = beta;
-      nfs::k_scale<double2><<<nb, 256, 0, c->stream>>>(w, 1.0 / beta, N);
-      nfs::k_scale<double2><<<nb, 256, 0, c->stream>>>(Mw, 1.0 / beta, N);
-      CK(cudaGetLastError());
-      CK(cudaMemcpyAsync(vec(V, j + 1), w, N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-      CK(cudaMemcpyAsync(vec(MV, j + 1), Mw, N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    }
-    // Rayleigh-Ritz on the projected matrix; theta = 1/omega, largest first
-    jacobi_eig(m, H, theta, Z);
-    order.resize(m);
-    for (int i = 0; i < m; ++i) order[i] = m - 1 - i;  // descending theta
-    nconv = 0;
-    for (int i = 0; i < nev; ++i) {
-      const int col = order[i];
-      const double res = std::fabs(beta_last * Z[(size_t)(m - 1) * m + col]);
-      if (res <= c->opt.eig_tol * std::fabs(theta[col])) ++nconv;
-    }
-    if (nconv == nev || restarts >= c->opt.max_restarts) {
-      if (nconv < nev) status = NFS_ENOCONV;
-      break;
-    }
-    // thick restart: keep the `keep` largest Ritz pairs
-    std::vector<double> Ycm((size_t)m * keep);
-    for (int i = 0; i < keep; ++i)
-      for (int r = 0; r < m; ++r) Ycm[(size_t)i * m + r] = Z[(size_t)r * m + order[i]];
-    TRY(rotate(c, V, m, Ycm, keep));
-    TRY(rotate(c, MV, m, Ycm, keep));
-    CK(cudaMemcpyAsync(vec(V, keep), vec(V, m), N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(vec(MV, keep), vec(MV, m), N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-    std::fill(H.begin(), H.end(), 0.0);
-    for (int i = 0; i < keep; ++i) {
-      H[(size_t)i * m + i] = theta[order[i]];
-      const double s = beta_last * Z[(size_t)(m - 1) * m + order[i]];
-      H[(size_t)keep * m + i] = H[(size_t)i * m + keep] = s;
-    }
-    jstart = keep;
-    ++restarts;
-  }
-  // results: omega ascending = theta descending (all wanted theta > 0)
-  double maxres = 0.0;
-  for (int i = 0; i < nev; ++i) {
-    const int col = order[i];
-    omega[i] = 1.0 / theta[col];
-    maxres = std::max(maxres, std::fabs(beta_last * Z[(size_t)(m - 1) * m + col]) / std::fabs(theta[col]));
-  }
-  if (Y) {
-    // Y[:, i] = V[0:m] z_i  (written through the rotation kernel into a copy)
-    std::vector<double> Ycm((size_t)m * nev);
-    for (int i = 0; i < nev; ++i)
-      for (int r = 0; r < m; ++r) Ycm[(size_t)i * m + r] = Z[(size_t)r * m + order[i]];
-    TRY(rotate(c, V, m, Ycm, nev));
-    CK(cudaMemcpyAsync(Y, V, (size_t)nev * N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  }
-  CK(cudaStreamSynchronize(c->stream));
-  if (info) {
-    info->lanczos_steps = steps;
-    info->restarts = restarts;
-    info->cg_iterations = cg_total;
-    info->matvecs_c64 = c->mv32 - mv32_0;
-    info->matvecs_c128 = c->mv64 - mv64_0;
-    info->nconv = nconv;
-    info->max_ritz_residual = maxres;
-    info->status = status;
-  }
-  return status;
+  TRY(join_caller(c));
+  return eigs_core(c, nev, omega, (double2*)Y, info);
 }
 
 extern "C" int nfs_eig_grad(nfs_ctx* c, int m, const double* weights, const void* Yv, double* d_eps,
                             double* d_gamma) {
   if (!c || m <= 0 || !weights || !Yv) return NFS_EINVAL;
-  if (c->has_mu) return NFS_EUNSUPPORTED;
+  if (c->has_mu || c->P != 1) return NFS_EUNSUPPORTED;
+  TRY(join_caller(c));
+  cudaStream_t s = c->work;
   const long long n = c->n, N = c->N;
-  if (d_eps) CK(cudaMemsetAsync(d_eps, 0, 3 * n * sizeof(double), c->stream));
-  if (d_gamma) CK(cudaMemsetAsync(d_gamma, 0, c->gam_len * sizeof(double), c->stream));
+  if (d_eps) CK(cudaMemsetAsync(d_eps, 0, 3 * n * sizeof(double), s));
+  if (d_gamma) CK(cudaMemsetAsync(d_gamma, 0, c->gam_len * sizeof(double), s));
   const double2* Y = (const double2*)Yv;
+  std::vector<double> yBy;
   for (int j = 0; j < m; ++j) {
     const double2* y = Y + (long long)j * N;
-    TRY(apply_Br(c, y, c->t64));
-    double yBy;
-    TRY(dot_re(c, y, c->t64, &yBy));
-    if (!(yBy != 0.0)) return NFS_EINVAL;
-    const double scale = weights[j] / ((double)n * yBy);
-    cudaError_t e = nfs::pass1_launch<double>(margs<double>(c, y, nullptr, nullptr));
+    nfs::k_apply_Br<<<grid_blocks(n, 256), 256, 0, s>>>(y, c->t64, c->lam64, c->n1, c->n2, c->n3, 1);
+    CK(cudaGetLastError());
+    TRY(dots_re(c, s, y, c->t64, yBy));
+    if (!(yBy[0] != 0.0)) return NFS_EINVAL;
+    const double scale = weights[j] / ((double)n * yBy[0]);
+    nfs::MatvecArgs<double> a = margs<double>(c, y, nullptr, nullptr);
+    a.stream = s;
+    cudaError_t e = nfs::pass1_launch<double>(a);
     if (e != cudaSuccess) return cuda_fail(e, "grad pass 1");
     nfs::GradArgs g{};
     g.fld = (const double2*)c->fld; g.tw3 = c->tw64[2];
     g.inv_phi = c->mat64; g.gam = c->mat64 + 3 * n;
     g.kind = c->kind; g.ax_a = c->ax_a; g.ax_b = c->ax_b;
     g.n1 = c->n1; g.n2 = c->n2; g.n3 = c->n3;
-    g.scale = scale; g.d_eps = d_eps; g.d_gamma = d_gamma; g.stream = c->stream;
+    g.scale = scale; g.d_eps = d_eps; g.d_gamma = d_gamma; g.stream = s;
     e = nfs::grad_launch(g);
     if (e != cudaSuccess) return cuda_fail(e, "grad launch");
   }
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaStreamSynchronize(s));
   return NFS_OK;
+}
+
+// --- batches -------------------------------------------------------------------
+
+extern "C" int nfs_setup_batch(nfs_batch** out, int nprob, const nfs_problem* probs, const nfs_options* opt) {
+  if (!out) return NFS_EINVAL;
+  *out = nullptr;
+  if (nprob <= 0 || !probs) return NFS_EINVAL;
+  const nfs_options o = resolved_options(opt);
+  TRY(check_options(o));
+  // group by (grid, medium kind, axis pair, mu present)
+  std::map<std::tuple<int, int, int, int, int, int, int>, std::vector<int>> groups;
+  for (int i = 0; i < nprob; ++i) {
+    const nfs_problem& p = probs[i];
+    const int ax_a = p.mat.kind == NFS_MEDIUM_PSEUDOCHIRAL ? p.mat.axis_a : 0;
+    const int ax_b = p.mat.kind == NFS_MEDIUM_PSEUDOCHIRAL ? p.mat.axis_b : 1;
+    groups[std::make_tuple(p.grid[0], p.grid[1], p.grid[2], p.mat.kind, ax_a, ax_b, p.mat.mu != nullptr ? 1 : 0)]
+        .push_back(i);
+  }
+  // every problem is validated on the host before any device memory is taken
+  struct ClassPrep {
+    std::vector<int> ids;
+    std::vector<const nfs_material*> ms;
+    std::vector<Prepared> prep;
+    double delta[3];
+  };
+  std::vector<ClassPrep> cls;
+  for (auto& kv : groups) {
+    ClassPrep cp;
+    cp.ids = kv.second;
+    const int P = (int)cp.ids.size();
+    std::vector<const double*> lat(P, nullptr), ks(P);
+    cp.ms.resize(P);
+    for (int q = 0; q < P; ++q) {
+      ks[q] = probs[cp.ids[q]].k;
+      cp.ms[q] = &probs[cp.ids[q]].mat;
+    }
+    TRY(prepare_class(P, probs[cp.ids[0]].grid, lat.data(), ks.data(), cp.ms.data(), o, cp.prep, cp.delta));
+    cls.push_back(std::move(cp));
+  }
+  nfs_batch* b = new (std::nothrow) nfs_batch();
+  if (!b) return NFS_ENOMEM;
+  b->where.assign(nprob, std::make_pair(-1, -1));
+  for (ClassPrep& cp : cls) {
+    const std::vector<int>& ids = cp.ids;
+    const int P = (int)ids.size();
+    nfs_ctx* c = nullptr;
+    const int rc = setup_class(&c, P, probs[ids[0]].grid, cp.ms.data(), cp.prep, cp.delta, o);
+    std::vector<Prepared>().swap(cp.prep);
+    if (rc != NFS_OK) {
+      nfs_destroy_batch(b);
+      return rc;
+    }
+    for (int q = 0; q < P; ++q) b->where[ids[q]] = std::make_pair((int)b->classes.size(), q);
+    b->classes.push_back(c);
+  }
+  *out = b;
+  return NFS_OK;
+}
+
+extern "C" int nfs_eigs_batch(nfs_batch* b, int nev, double* omega, nfs_eigs_info* info) {
+  if (!b || !omega || nev <= 0) return NFS_EINVAL;
+  const int nc = (int)b->classes.size();
+  std::vector<std::vector<double>> om(nc);
+  std::vector<std::vector<nfs_eigs_info>> inf(nc);
+  std::vector<int> rc(nc, NFS_OK);
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  for (int i = 0; i < nc; ++i) {
+    nfs_ctx* c = b->classes[i];
+    if (nev >= c->N / 2) return NFS_EINVAL;
+    om[i].assign((size_t)c->P * nev, 0.0);
+    inf[i].assign(c->P, nfs_eigs_info{});
+    TRY(join_caller(c));
+  }
+  // one host thread per grid class; each drives its own stream
+  std::vector<std::thread> th;
+  for (int i = 0; i < nc; ++i)
+    th.emplace_back([&, i]() {
+      cudaSetDevice(dev);
+      rc[i] = eigs_core(b->classes[i], nev, om[i].data(), nullptr, inf[i].data());
+    });
+  for (auto& t : th) t.join();
+  int worst = NFS_OK;
+  for (int i = 0; i < nc; ++i)
+    if (rc[i] != NFS_OK && (worst == NFS_OK || rc[i] != NFS_ENOCONV)) worst = rc[i];
+  if (worst != NFS_OK && worst != NFS_ENOCONV) return worst;
+  const int nprob = (int)b->where.size();
+  for (int pi = 0; pi < nprob; ++pi) {
+    const int ci = b->where[pi].first, q = b->where[pi].second;
+    std::copy(om[ci].begin() + (size_t)q * nev, om[ci].begin() + (size_t)(q + 1) * nev, omega + (size_t)pi * nev);
+    if (info) info[pi] = inf[ci][q];
+  }
+  return worst;
+}
+
+extern "C" int nfs_batch_num_classes(const nfs_batch* b) { return b ? (int)b->classes.size() : 0; }
+
+extern "C" void nfs_destroy_batch(nfs_batch* b) {
+  if (!b) return;
+  for (nfs_ctx* c : b->classes) nfs_destroy(c);
+  delete b;
 }

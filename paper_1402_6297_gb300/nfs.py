@@ -43,6 +43,7 @@ EXPORTED = (
     "nfs_default_options", "nfs_setup", "nfs_matvec", "nfs_matvec_passes", "nfs_apply_Br", "nfs_cg_solve",
     "nfs_eigs", "nfs_eig_grad", "nfs_num_voxels", "nfs_device_bytes", "nfs_set_stream",
     "nfs_destroy", "nfs_strerror", "nfs_matvec_noalloc",
+    "nfs_setup_batch", "nfs_eigs_batch", "nfs_batch_num_classes", "nfs_destroy_batch",
 )
 NOALLOC_MAX_VOXELS = 32768
 
@@ -107,6 +108,14 @@ class EigsInfo(ctypes.Structure):
     ]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("grid", ctypes.c_int * 3),
+        ("k", ctypes.c_double * 3),
+        ("mat", Material),
+    ]
+
+
 _lib = None
 
 
@@ -148,6 +157,14 @@ def lib():
     L.nfs_matvec_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ip, ip, ip,
                                       vp, vp, dp, dp, vp, vp, vp]
     L.nfs_matvec_noalloc.restype = ip
+    L.nfs_setup_batch.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(Problem), ctypes.POINTER(Options)]
+    L.nfs_setup_batch.restype = ip
+    L.nfs_eigs_batch.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(EigsInfo)]
+    L.nfs_eigs_batch.restype = ip
+    L.nfs_batch_num_classes.argtypes = [vp]
+    L.nfs_batch_num_classes.restype = ip
+    L.nfs_destroy_batch.argtypes = [vp]
+    L.nfs_destroy_batch.restype = None
     L.nfs_strerror.argtypes = [ip]
     L.nfs_strerror.restype = ctypes.c_char_p
     _ = dp
@@ -177,6 +194,20 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _material(medium):
+    """nfs_material over host copies of the medium (returned to keep alive)."""
+    eps = np.ascontiguousarray(medium.eps, dtype=np.float64)
+    gam = np.ascontiguousarray(medium.gamma, dtype=np.float64)
+    mu = None if medium.mu is None else np.ascontiguousarray(medium.mu, dtype=np.float64)
+    m = Material()
+    m.kind = MEDIUM_CHIRAL if medium.kind == "chiral" else MEDIUM_PSEUDOCHIRAL
+    m.axis_a, m.axis_b = (int(medium.axes[0]), int(medium.axes[1]))
+    m.eps = _dptr(eps)
+    m.gamma = _dptr(gam)
+    m.mu = _dptr(mu) if mu is not None else ctypes.POINTER(ctypes.c_double)()
+    return m, (eps, gam, mu)
+
+
 def _current_stream():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -201,16 +232,7 @@ class Context:
         o.stream = self.stream_handle
         self.options = o
         self.precision = precision
-        eps = np.ascontiguousarray(medium.eps, dtype=np.float64)
-        gam = np.ascontiguousarray(medium.gamma, dtype=np.float64)
-        mu = None if medium.mu is None else np.ascontiguousarray(medium.mu, dtype=np.float64)
-        m = Material()
-        m.kind = MEDIUM_CHIRAL if medium.kind == "chiral" else MEDIUM_PSEUDOCHIRAL
-        m.axis_a, m.axis_b = (int(medium.axes[0]), int(medium.axes[1]))
-        m.eps = _dptr(eps)
-        m.gamma = _dptr(gam)
-        m.mu = _dptr(mu) if mu is not None else ctypes.POINTER(ctypes.c_double)()
-        self._keep = (eps, gam, mu)
+        m, self._keep = _material(medium)
         a = float(getattr(medium, "a", 1.0))
         lattice = np.diag([a, a, a]).astype(np.float64).ravel()
         # kdota = (k.a_1, k.a_2, k.a_3); for a lattice a_l = a e_l, k = kdota / a
@@ -315,6 +337,68 @@ class Context:
                                   ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_gam.data_ptr())),
                "nfs_eig_grad")
         return d_eps, d_gam
+
+
+class Batch:
+    """Many independent Bloch problems solved together (nfs_setup_batch).
+
+    problems: sequence of (grid, kdota, medium) on the unit cube lattice.
+    Problems sharing a grid, medium kind, pseudochiral axes and mu-ness are
+    solved in lock-step through single kernel launches; distinct classes run
+    concurrently."""
+
+    def __init__(self, problems, precision="mixed", stream=None, **opts):
+        import torch  # noqa: F401  (device and stream owner)
+        L = lib()
+        self.nprob = len(problems)
+        arr = (Problem * max(1, self.nprob))()
+        keep = []
+        for i, (grid, kdota, medium) in enumerate(problems):
+            if float(getattr(medium, "a", 1.0)) != 1.0:
+                raise ValueError("batched problems use the unit cube lattice")
+            m, kp = _material(medium)
+            keep.append(kp)
+            arr[i].grid[:] = [int(x) for x in grid]
+            arr[i].k[:] = [float(x) for x in kdota]
+            arr[i].mat = m
+        o = default_options()
+        o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        for key, val in opts.items():
+            setattr(o, key, val)
+        o.stream = stream if stream is not None else _current_stream()
+        h = ctypes.c_void_p()
+        _check(L.nfs_setup_batch(ctypes.byref(h), int(self.nprob), arr, ctypes.byref(o)), "nfs_setup_batch")
+        self.h = h
+
+    @property
+    def num_classes(self):
+        return int(lib().nfs_batch_num_classes(self.h))
+
+    def eigs(self, nev, allow_noconv=False):
+        """(omega [nprob, nev], list of EigsInfo)."""
+        omega = np.zeros((self.nprob, nev), dtype=np.float64)
+        infos = (EigsInfo * max(1, self.nprob))()
+        code = lib().nfs_eigs_batch(self.h, int(nev), _dptr(omega), infos)
+        if code != NFS_OK and not (allow_noconv and code == NFS_ENOCONV):
+            raise NFSError(code, "nfs_eigs_batch")
+        return omega, [infos[i] for i in range(self.nprob)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nfs_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def matvec_noalloc(grid, kdota, kind, axes, eps, gamma, u, out, alpha=2.0, beta=3.0, stream=None):

@@ -51,6 +51,7 @@ def test_struct_layouts_match_header(nfs):
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(nfs_options), sizeof(nfs_material), sizeof(nfs_solve_info), sizeof(nfs_eigs_info));
   printf("%zu %zu %zu\n", offsetof(nfs_options, seed), offsetof(nfs_options, stream), offsetof(nfs_eigs_info, max_ritz_residual));
+  printf("%zu %zu %zu\n", sizeof(nfs_problem), offsetof(nfs_problem, k), offsetof(nfs_problem, mat));
   return 0;
 }
 """
@@ -68,6 +69,9 @@ int main(void) {
     assert sizes[4] == nfs.Options.seed.offset
     assert sizes[5] == nfs.Options.stream.offset
     assert sizes[6] == nfs.EigsInfo.max_ritz_residual.offset
+    assert sizes[7] == ctypes.sizeof(nfs.Problem)
+    assert sizes[8] == nfs.Problem.k.offset
+    assert sizes[9] == nfs.Problem.mat.offset
 
 
 def test_default_options(nfs):
@@ -131,3 +135,45 @@ def test_null_handles_rejected(nfs):
     assert L.nfs_eigs(None, 3, None, None, None) == nfs.NFS_EINVAL
     assert L.nfs_eig_grad(None, 1, None, None, None, None) == nfs.NFS_EINVAL
     L.nfs_destroy(None)
+
+
+def _batch_code(nfs, problems, **opt):
+    """nfs_setup_batch over (grid, k, medium) tuples; returns the code."""
+    L = nfs.lib()
+    arr = (nfs.Problem * len(problems))()
+    keep = []
+    for i, (grid, k, med) in enumerate(problems):
+        m, kp = nfs._material(med)
+        keep.append(kp)
+        arr[i].grid[:] = list(grid)
+        arr[i].k[:] = list(k)
+        arr[i].mat = m
+    o = nfs.default_options()
+    for key, v in opt.items():
+        setattr(o, key, v)
+    h = ctypes.c_void_p()
+    code = L.nfs_setup_batch(ctypes.byref(h), len(problems), arr, ctypes.byref(o))
+    assert not h.value
+    return code
+
+
+def test_batch_validation_errors_without_gpu(nfs):
+    """A batch is validated problem by problem on the host before any device
+    memory is taken: one bad problem anywhere fails the whole batch."""
+    L = nfs.lib()
+    g = (8, 8, 8)
+    good = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+    g16 = (16, 16, 16)
+    good16 = wl.chiral_sphere(g16, 0.25, 13.0, 1.0, 0.5)
+    ok = [(g, (0.1, 0.2, 0.3), good), (g16, (0.2, 0.1, 0.3), good16)]
+    assert _batch_code(nfs, ok + [(g, (0.0, 0.0, 0.0), good)]) == nfs.NFS_EKPOINT
+    bad = wl.chiral_sphere(g16, 0.25, 13.0, 1.0, 3.7)
+    assert _batch_code(nfs, ok + [(g16, (0.1, 0.2, 0.3), bad)]) == nfs.NFS_ENOTHPD
+    assert _batch_code(nfs, ok + [((10, 10, 10), (0.1, 0.2, 0.3), wl.homogeneous((10, 10, 10)))]) \
+        == nfs.NFS_EUNSUPPORTED
+    assert _batch_code(nfs, ok, cg_tol=-1.0) == nfs.NFS_EINVAL
+    h = ctypes.c_void_p()
+    assert L.nfs_setup_batch(ctypes.byref(h), 0, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_eigs_batch(None, 3, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_batch_num_classes(None) == 0
+    L.nfs_destroy_batch(None)

@@ -1,0 +1,84 @@
+"""The differentiable eigenvalue function (autograd over nfs_eig_grad) against
+central finite differences of the GPU eigenvalues and against the oracle.
+
+A per-voxel difference with step 1e-6 is below the eigenvalue accuracy
+(d omega / d eps_v ~ omega / n), so the finite-difference checks are
+directional: grad . d against [f(p + h d) - f(p - h d)] / 2h with a dense
+random direction d, plus a per-voxel check with a larger step.  The
+directional step is h = 1e-4: with |grad . d| ~ 1e-2 a step of 1e-6 would need
+the eigenvalue sums to ~1e-15 absolute, below what an iterative solve at
+tolerance 1e-13 reproduces between runs, while h = 1e-4 keeps the O(h^2)
+truncation near 1e-8 relative."""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import gep
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+K = (0.1, 0.2, 0.3)
+
+
+@pytest.fixture(scope="module")
+def ag(lib):
+    from paper_1402_6297_gb300 import autograd
+    return autograd
+
+
+def f_sum(ag, eps, gam, g, nev=5):
+    return float(ag.chiral_eigenvalues(eps, gam, g, K, nev=6, eig_tol=1e-12, cg_tol=1e-13)[:nev].sum())
+
+
+def test_directional_derivative_matches_central_difference(ag):
+    g = (16, 16, 16)
+    med = wl.smoothed_chiral_field(g, seed=2, sigma=0.1)
+    eps = torch.tensor(med.eps[0], dtype=torch.float64, requires_grad=True)
+    gam = torch.tensor(med.gamma[0], dtype=torch.float64, requires_grad=True)
+    om = ag.chiral_eigenvalues(eps, gam, g, K, nev=6, eig_tol=1e-12, cg_tol=1e-13)
+    assert om[4] < om[5] * (1 - 1e-6)  # the summed cluster is complete
+    om[:5].sum().backward()
+    rng = np.random.default_rng(0)
+    for which in ("eps", "gamma"):
+        d = torch.tensor(rng.standard_normal(eps.shape))
+        h = 1e-4
+        base_e, base_g = eps.detach(), gam.detach()
+        if which == "eps":
+            fp = f_sum(ag, base_e + h * d, base_g, g)
+            fm = f_sum(ag, base_e - h * d, base_g, g)
+            an = float((eps.grad * d).sum())
+        else:
+            fp = f_sum(ag, base_e, base_g + h * d, g)
+            fm = f_sum(ag, base_e, base_g - h * d, g)
+            an = float((gam.grad * d).sum())
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-9, (which, fd, an)
+
+
+def test_per_voxel_gradient_large_step(ag):
+    g = (8, 8, 8)
+    med = wl.smoothed_chiral_field(g, seed=7, sigma=0.15)
+    eps = torch.tensor(med.eps[0], dtype=torch.float64, requires_grad=True)
+    gam = torch.tensor(med.gamma[0], dtype=torch.float64, requires_grad=True)
+    om = ag.chiral_eigenvalues(eps, gam, g, K, nev=3, eig_tol=1e-12, cg_tol=1e-13)
+    om[0].backward()
+    # oracle: pencil perturbation formula, summed over the three components
+    w, z, idx = gep.dense_eigs(g, K, med)
+    re, rg = gep.pencil_gradient(med, w[[idx[0]]], z[:, [idx[0]]])
+    assert np.abs(eps.grad.numpy() - re.sum(0)).max() < 1e-6 * np.abs(re.sum(0)).max()
+    assert np.abs(gam.grad.numpy() - rg.sum(0)).max() < 1e-6 * np.abs(rg.sum(0)).max()
+    # per-voxel central differences with h = 1e-3 (second-order error ~ h^2)
+    rng = np.random.default_rng(1)
+    for _ in range(4):
+        v = tuple(int(x) for x in rng.integers(0, 8, size=3))
+        h = 1e-3
+        e2 = eps.detach().clone()
+        e2[v] += h
+        fp = float(ag.chiral_eigenvalues(e2, gam.detach(), g, K, nev=3, eig_tol=1e-12, cg_tol=1e-13)[0])
+        e2[v] -= 2 * h
+        fm = float(ag.chiral_eigenvalues(e2, gam.detach(), g, K, nev=3, eig_tol=1e-12, cg_tol=1e-13)[0])
+        fd = (fp - fm) / (2 * h)
+        an = float(eps.grad[v])
+        assert abs(fd - an) <= 1e-4 * abs(an) + 1e-10, (v, fd, an)
