@@ -108,6 +108,9 @@ typedef struct {
   int nconv;               /* wanted Ritz pairs that met eig_tol                   */
   double max_ritz_residual;/* max over returned pairs of |beta y_m| / |theta|      */
   int status;
+  long long kernel_launches; /* kernels the library launched during the call (CUDA
+                              * graph nodes included); in a batch, those of the
+                              * problem's whole class                                */
 } nfs_eigs_info;
 
 /* Defaults: FP64, alpha = 2, beta = 3, cg_tol 1e-12, cg_maxit 2000,

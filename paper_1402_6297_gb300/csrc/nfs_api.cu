@@ -87,6 +87,7 @@ struct nfs_ctx {
   std::vector<GraphEntry> graphs;
   long long bytes = 0;
   long long mv32 = 0, mv64 = 0;
+  long long launches = 0;  // kernels this context has launched (graph nodes included)
 };
 
 struct nfs_batch {
@@ -195,6 +196,7 @@ int matvec(nfs_ctx* c, cudaStream_t s, const nfs::cplx<R>* u, nfs::cplx<R>* Au, 
   a.bs.sskip = sskip;
   cudaError_t e = nfs::matvec_launch<R>(a);
   if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
+  c->launches += 3;
   if (sizeof(R) == 4) c->mv32 += c->P; else c->mv64 += c->P;
   return NFS_OK;
 }
@@ -222,6 +224,7 @@ template <typename C>
 int dots_re(nfs_ctx* c, cudaStream_t s, const C* x, const C* y, std::vector<double>& out) {
   nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(x, y, c->N, c->dscratch, kRedBlocks, nullptr, 0);
   CK(cudaGetLastError());
+  c->launches += 1;
   CK(cudaMemcpyAsync(c->hscratch, c->dscratch, (size_t)kRedBlocks * c->P * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out.assign(c->P, 0.0);
@@ -331,11 +334,13 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
   TRY(put_small(c, s, 0, tol2));
   nfs::k_cg_init<<<c->P, kRedThreads, 0, s>>>(c->st, c->d_small, maxit, 6 * c->n3);
   CK(cudaGetLastError());
+  c->launches += 2;
   cudaGraphExec_t exec = nullptr;
   TRY(cg_chunk_graph<R>(c, x, r, p, Ap, &exec));
   const size_t head = offsetof(CGState, part_a);
   for (;;) {
     CK(cudaGraphLaunch(exec, s));
+    c->launches += 5 * kCgChunk;
     CK(cudaMemcpy2DAsync(c->st_host, sizeof(CGState), c->st, sizeof(CGState), head, c->P, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     bool all = true;
@@ -357,6 +362,7 @@ int sub64(nfs_ctx* c, cudaStream_t s, const double2* a, const double2* b, double
   const long long tot = c->P * c->N;
   nfs::k_sub<double2><<<grid_blocks(tot, 256), 256, 0, s>>>(a, b, y, tot);
   CK(cudaGetLastError());
+  c->launches += 1;
   return NFS_OK;
 }
 
@@ -427,12 +433,14 @@ int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, const std::vect
     TRY(put_small(c, s, P, inv));
     nfs::k_demote<<<nb, 256, 0, s>>>(c->r64, c->d_small + P, c->r32, c->N, tot);
     CK(cudaGetLastError());
+    c->launches += 1;
     CK(cudaMemsetAsync(c->x32, 0, tot * sizeof(float2), s));
     std::vector<int> it, st;
     TRY(cg_run<float>(c, c->x32, c->r32, c->p32, c->Ap32, itol2, c->opt.cg_maxit, it, st));
     TRY(put_small(c, s, 2 * P, nrm));
     nfs::k_axpy_promote<<<nb, 256, 0, s>>>(x, c->d_small + 2 * P, c->x32, c->N, tot);
     CK(cudaGetLastError());
+    c->launches += 1;
     // refinement residual with the complex128 product, skipping finished problems
     TRY(put_flags(c, s, P, skip));
     TRY(matvec<double>(c, s, x, c->Ap64, c->d_flags + P, 1));
@@ -472,6 +480,7 @@ int multi_dot(nfs_ctx* c, const double2* Vbase, int j0, int m, const double2* w,
                                                                               m, w, c->N, part, d_active);
   nfs::k_multi_dot_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
   CK(cudaGetLastError());
+  c->launches += 2;
   CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out.assign(c->hscratch, c->hscratch + (size_t)c->P * 2 * m);
@@ -489,6 +498,7 @@ int multi_axpy(nfs_ctx* c, double2* w, double2* Mw, int j0, int m, const std::ve
   nfs::k_multi_axpy<<<dim3(grid_blocks(c->N, 256), c->P), 256, 0, s>>>(
       w, Mw, c->V + (long long)j0 * c->N, c->MV + (long long)j0 * c->N, vstride, dcoef, m, c->N, d_active);
   CK(cudaGetLastError());
+  c->launches += 1;
   CK(cudaStreamSynchronize(s));  // the pinned staging buffer is reused next
   return NFS_OK;
 }
@@ -505,6 +515,7 @@ int shadow_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, c
                                                                                         c->N, part, d_active);
   nfs::k_dots_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
   CK(cudaGetLastError());
+  c->launches += 3;
   CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out.assign(c->hscratch, c->hscratch + (size_t)c->P * 2 * m);
@@ -519,6 +530,7 @@ int refresh_shadows(nfs_ctx* c, int first, int count) {
   nfs::k_to_c64<<<nb, 256, 0, c->work>>>(c->V + off, vstride, c->V32 + off, vstride, len, c->P);
   nfs::k_to_c64<<<nb, 256, 0, c->work>>>(c->MV + off, vstride, c->MV32 + off, vstride, len, c->P);
   CK(cudaGetLastError());
+  c->launches += 2;
   return NFS_OK;
 }
 
@@ -558,6 +570,7 @@ int rotate(nfs_ctx* c, double2* base, int m, const std::vector<double>& Y, int k
   nfs::k_rotate_basis<TE><<<dim3(grid_blocks((c->N + TE - 1) / TE, 1), c->P), 256, smem, c->work>>>(
       base, (long long)c->vcap * c->N, m, c->dY, k, c->N, d_active);
   CK(cudaGetLastError());
+  c->launches += 1;
   CK(cudaStreamSynchronize(c->work));  // Y's host buffer may be released next
   return NFS_OK;
 }
@@ -572,6 +585,7 @@ int apply_Br_basis(nfs_ctx* c, int j, double2* out) {
   nfs::k_apply_Br<<<grid_blocks(c->n * c->P, 256), 256, 0, c->work>>>(c->t64, out, c->lam64, c->n1, c->n2, c->n3,
                                                                       c->P);
   CK(cudaGetLastError());
+  c->launches += 1;
   return NFS_OK;
 }
 
@@ -601,13 +615,14 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
   TRY(ensure_scratch(c, lanczos_scratch_len(P, c->vcap)));
   const long long vstride = (long long)c->vcap * N;
   cudaStream_t s = c->work;
-  const long long mv32_0 = c->mv32, mv64_0 = c->mv64;
+  const long long mv32_0 = c->mv32, mv64_0 = c->mv64, launches_0 = c->launches;
   const int nb = grid_blocks(P * N, 256);
   auto col = [&](double2* base, int p, int j) { return base + p * vstride + (long long)j * N; };
 
   // starting vectors, A_r-normalised (vector 0 of every basis)
   nfs::k_random_fill<<<nb, 256, 0, s>>>(c->V, N, vstride, P, c->opt.seed);
   CK(cudaGetLastError());
+  c->launches += 1;
   for (int p = 0; p < P; ++p)
     CK(cudaMemcpyAsync(c->t64 + p * N, col(c->V, p, 0), N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
   TRY(matvec<double>(c, s, c->t64, c->t64b));
@@ -622,6 +637,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
   nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(c->t64, c->t64b, c->d_small + P, c->V, c->MV, c->V32, c->MV32, vstride,
                                                0, N, P, nullptr);
   CK(cudaGetLastError());
+  c->launches += 1;
 
   const int keep = std::min(m - 1, std::max(nev + 1, nev + (m - nev) / 2));
   const int check_every = 10;
@@ -722,6 +738,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(w, Mw, c->d_small + P, c->V, c->MV, c->V32, c->MV32, vstride,
                                                    j + 1, N, P, d_active);
       CK(cudaGetLastError());
+      c->launches += 1;
       local_lo = j;
       // Ritz values of the leading (j+1) x (j+1) block; residual |beta z_last|
       const int k = j + 1;
@@ -820,6 +837,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       in.nconv = status[p] == NFS_OK ? nev : nconv[p];
       in.max_ritz_residual = maxres;
       in.status = status[p];
+      in.kernel_launches = c->launches - launches_0;
     }
     if (status[p] != NFS_OK) worst = status[p];
   }

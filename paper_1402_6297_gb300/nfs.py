@@ -105,6 +105,7 @@ class EigsInfo(ctypes.Structure):
         ("nconv", ctypes.c_int),
         ("max_ritz_residual", ctypes.c_double),
         ("status", ctypes.c_int),
+        ("kernel_launches", ctypes.c_longlong),
     ]
 
 
