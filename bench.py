@@ -271,7 +271,7 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     stream = torch.cuda.current_stream()
 
-    ctx = nfs.Context(grid, kd, med, precision="mixed", cg_tol=1e-10, eig_tol=1e-9)
+    ctx = nfs.Context(grid, kd, med, precision="mixed", cg_tol=1e-10, eig_tol=1e-10)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # ---- A_r products: whole product and each pass, CUDA events on the stream
@@ -381,7 +381,7 @@ def run_ours(args):
     for i in range(0 if args.skip_e2e else max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        c2 = nfs.Context(grid, kd, med_pinned, precision="mixed", cg_tol=1e-10, eig_tol=1e-9)
+        c2 = nfs.Context(grid, kd, med_pinned, precision="mixed", cg_tol=1e-10, eig_tol=1e-10)
         om2, _, _ = c2.eigs(NEV, vectors=False, allow_noconv=True)
         c2.close()
         torch.cuda.synchronize()
@@ -412,7 +412,11 @@ def run_ours(args):
                        "cg_iterations": int(cg_its), "matvecs_c64": int(info.matvecs_c64),
                        "matvecs_c128": int(info.matvecs_c128), "nconv": info.nconv,
                        "max_residual": max(res), "omega": [float(x) for x in omega],
-                       "host_s": host_s},
+                       "host_s": host_s,
+                       "split_s": {"total": info.seconds_total, "cg": info.seconds_cg,
+                                   "refine": info.seconds_refine, "ritz": info.seconds_ritz,
+                                   "lanczos": info.seconds_total - info.seconds_cg - info.seconds_refine
+                                   - info.seconds_ritz}},
         "fp64": fp64,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -88,6 +88,10 @@ typedef struct {
   double eig_tol;          /* Lanczos: Ritz residual <= eig_tol * |theta|         */
   int ncv;                 /* Lanczos basis size; 0 means max(3 nev, 2 nev + 2)   */
   int max_restarts;        /* thick-restart cap                                   */
+  double orth_tol;         /* Lanczos semi-orthogonality level: when the measured
+                            * loss of A_r-orthogonality of a new vector to the
+                            * older basis exceeds it, those components are
+                            * removed; 0 = every step.  Default 1e-10            */
   unsigned long long seed; /* starting-vector seed                                */
   void* stream;            /* cudaStream_t for every launch; NULL = default       */
 } nfs_options;
@@ -111,6 +115,17 @@ typedef struct {
   long long kernel_launches; /* kernels the library launched during the call (CUDA
                               * graph nodes included); in a batch, those of the
                               * problem's whole class                                */
+  /* host wall-clock split of the call (the class's, in a batch): total; inside
+   * the CG iteration loops; the rest of the linear solves (residual
+   * refinement); host projected eigensolves; then the Lanczos phases. */
+  double seconds_total;
+  double seconds_cg;
+  double seconds_refine;
+  double seconds_ritz;
+  double seconds_recurrence; /* three-term recurrence (FP64)                       */
+  double seconds_orth;       /* orthogonality monitor and re-orthogonalisation     */
+  double seconds_vectors;    /* forming the returned Ritz vectors                  */
+  int reorthogonalisations;  /* steps that re-orthogonalised                       */
 } nfs_eigs_info;
 
 /* Defaults: FP64, alpha = 2, beta = 3, cg_tol 1e-12, cg_maxit 2000,

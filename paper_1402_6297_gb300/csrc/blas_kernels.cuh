@@ -402,78 +402,81 @@ __global__ void k_rotate_basis(double2* __restrict__ V, long long vstride, int m
   }
 }
 
-// ---------------------------------------------------------------------------
-// Orthogonality monitor: inner products of a new Lanczos vector with complex64
-// shadow copies of A_r V.  They measure the basis's loss of orthogonality to
-// about 1e-7 / sqrt(N) (single-precision products, FP64 block sums), which is
-// enough to decide when an exact FP64 re-orthogonalisation is due; they never
-// enter the basis or the projected matrix.  Shadows are laid out like the FP64
-// basis (vstride per problem, N per vector).
-// ---------------------------------------------------------------------------
-
-// y[p * ystride + i] = complex64(a[p * astride + i]), i < len, p < P
-__global__ void k_to_c64(const double2* __restrict__ a, long long astride, float2* __restrict__ y, long long ystride,
-                         long long len, int P) {
-  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < len * P; g += (long long)gridDim.x * blockDim.x) {
-    const long long p = g / len, i = g % len;
-    const double2 v = a[p * astride + i];
-    y[p * ystride + i] = make_float2((float)v.x, (float)v.y);
-  }
-}
-
-// part[(((p * m + j) * gridDim.x) + b) * 2 + {0, 1}] = block b's share of
-// conj(S_pj)^T w32_p for the G vectors j = blockIdx.y * G + g < m; grid
-// (kRedBlocks, ceil(m / G), P).
-template <int G>
-__global__ void __launch_bounds__(kRedThreads)
-k_shadow_dots(const float2* __restrict__ S, long long sstride, int m, const float2* __restrict__ w32, long long N,
-              double* __restrict__ part, const int* __restrict__ active) {
-  const int p = blockIdx.z;
+// Re-orthogonalisation through the shadows: w_p -= sum_j d_pj V32_pj and
+// Mw_p -= sum_j d_pj MV32_pj for j < m, with d (layout of k_dots_finish, on the
+// device) exact A_r inner products.  It runs only when the loss of
+// orthogonality is small (|d| ~ 1e-8 of |w|), so the update is formed in FP32
+// arithmetic from the FP32 shadows: its error is ~1e-8 * 6e-8 of |w|.
+// Grid (blocks, P); problems with a zero flag are skipped.
+__global__ void k_shadow_axpy(double2* __restrict__ w, double2* __restrict__ Mw, const float2* __restrict__ V32,
+                              const float2* __restrict__ MV32, long long vstride, const double* __restrict__ d, int m,
+                              long long N, const int* __restrict__ active) {
+  const int p = blockIdx.y;
   if (active && !active[p]) return;
-  S += (long long)p * sstride;
-  w32 += (long long)p * N;
-  const int j0 = blockIdx.y * G;
-  float re[G], im[G];
-  double dre[G], dim[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) {
-    re[g] = im[g] = 0.f;
-    dre[g] = dim[g] = 0.0;
-  }
-  int cnt = 0;
-  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
-    const float2 b = w32[i];
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      if (j0 + g < m) {
-        const float2 a = S[(long long)(j0 + g) * N + i];
-        re[g] += a.x * b.x + a.y * b.y;
-        im[g] += a.x * b.y - a.y * b.x;
-      }
+  w += (long long)p * N;
+  Mw += (long long)p * N;
+  V32 += (long long)p * vstride;
+  MV32 += (long long)p * vstride;
+  d += (long long)p * m * 2;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int j = 0; j < m; ++j) {
+      const float2 cj = make_float2((float)d[2 * j], (float)d[2 * j + 1]);
+      const float2 v = V32[(long long)j * N + i], mv = MV32[(long long)j * N + i];
+      a = cadd(a, cmul(cj, v));
+      b = cadd(b, cmul(cj, mv));
     }
-    if (++cnt == 16) {  // fold short single-precision runs into FP64
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        dre[g] += re[g];
-        dim[g] += im[g];
-        re[g] = im[g] = 0.f;
-      }
-      cnt = 0;
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < G; ++g) {
-    const double sr = block_sum<kRedThreads>(dre[g] + re[g]);
-    const double si = block_sum<kRedThreads>(dim[g] + im[g]);
-    if (threadIdx.x == 0 && j0 + g < m) {
-      const long long o = (((long long)p * m + j0 + g) * gridDim.x + blockIdx.x) * 2;
-      part[o] = sr;
-      part[o + 1] = si;
-    }
+    double2 wi = w[i], mi = Mw[i];
+    wi.x -= (double)a.x;
+    wi.y -= (double)a.y;
+    mi.x -= (double)b.x;
+    mi.y -= (double)b.y;
+    w[i] = wi;
+    Mw[i] = mi;
   }
 }
 
-// out[(p * m + j) * 2 + {0,1}] = sum over nb blocks; grid (m, P)
+// ---------------------------------------------------------------------------
+// Exact A_r inner products on the FP32 units.  A_r is ill-conditioned
+// (|A v| |w| >> |v|_A |w|_A), so single-precision inner products carry an
+// absolute error near 1e-8 |w|_A: the level of orthogonality Lanczos needs to
+// keep.  Here every operand is split into two floats (hi + lo, the lo part
+// holding the FP64 remainder), the hi x hi products are formed exactly
+// (TwoProduct by FMA) and summed exactly (TwoSum, Knuth), the small hi x lo
+// and lo x hi terms and the rounding errors go to an ordinary FP32 sum, and
+// the block sums are FP64: about 1e-14 of sum |terms|.  Double-precision
+// arithmetic, scarce on this GPU, is used only for the per-block totals.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// s + e = a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// running sum hi + lo (exact additions into hi, errors into lo)
+struct DSAcc {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    two_sum(hi, x, hi, e);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ float2 split_lo(double2 v, float2 hi) {
+  return make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+}
+
+// out[(p * m + j) * 2 + {0,1}] = sum over the nb block partials of k_exact_dots; grid (m, P)
 __global__ void __launch_bounds__(kRedThreads)
 k_dots_finish(const double* __restrict__ part, int m, int nb, double* __restrict__ out, const int* __restrict__ active) {
   const int j = blockIdx.x, p = blockIdx.y;
@@ -491,12 +494,75 @@ k_dots_finish(const double* __restrict__ part, int m, int nb, double* __restrict
   }
 }
 
+// part[(((p * m + j) * gridDim.x) + b) * 2 + {0, 1}] = block b's share of
+// conj(S_pj)^T w_p (S = Shi + Slo) for the G vectors j = blockIdx.y * G + g < m;
+// grid (kRedBlocks, ceil(m / G), P).  w is FP64 and split here.
+template <int G>
+__global__ void __launch_bounds__(kRedThreads)
+k_exact_dots(const float2* __restrict__ Shi, const float2* __restrict__ Slo, long long sstride, int m,
+             const double2* __restrict__ w, long long N, double* __restrict__ part, const int* __restrict__ active) {
+  const int p = blockIdx.z;
+  if (active && !active[p]) return;
+  Shi += (long long)p * sstride;
+  Slo += (long long)p * sstride;
+  w += (long long)p * N;
+  const int j0 = blockIdx.y * G;
+  DSAcc re[G], im[G];
+  float sre[G], sim[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) sre[g] = sim[g] = 0.f;
+  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
+    const double2 wd = w[i];
+    const float2 bh = make_float2((float)wd.x, (float)wd.y);
+    const float2 bl = split_lo(wd, bh);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      if (j0 + g < m) {
+        const float2 ah = Shi[(long long)(j0 + g) * N + i], al = Slo[(long long)(j0 + g) * N + i];
+        // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
+        float p1, e1, p2, e2, p3, e3, p4, e4;
+        two_prod(ah.x, bh.x, p1, e1);
+        two_prod(ah.y, bh.y, p2, e2);
+        two_prod(ah.x, bh.y, p3, e3);
+        two_prod(ah.y, bh.x, p4, e4);
+        re[g].add(p1);
+        re[g].add(p2);
+        im[g].add(p3);
+        im[g].add(-p4);
+        float t = e1 + e2;
+        t = __fmaf_rn(ah.x, bl.x, t);
+        t = __fmaf_rn(al.x, bh.x, t);
+        t = __fmaf_rn(ah.y, bl.y, t);
+        t = __fmaf_rn(al.y, bh.y, t);
+        sre[g] += t;
+        float u = e3 - e4;
+        u = __fmaf_rn(ah.x, bl.y, u);
+        u = __fmaf_rn(al.x, bh.y, u);
+        u = __fmaf_rn(-ah.y, bl.x, u);
+        u = __fmaf_rn(-al.y, bh.x, u);
+        sim[g] += u;
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const double sr = block_sum<kRedThreads>(re[g].value() + (double)sre[g]);
+    const double si = block_sum<kRedThreads>(im[g].value() + (double)sim[g]);
+    if (threadIdx.x == 0 && j0 + g < m) {
+      const long long o = (((long long)p * m + j0 + g) * gridDim.x + blockIdx.x) * 2;
+      part[o] = sr;
+      part[o + 1] = si;
+    }
+  }
+}
+
 // New basis vector j of every active problem: V_pj = s_p w_p, MV_pj = s_p Mw_p
-// in FP64, plus their complex64 shadows.
+// in FP64, plus their complex64 shadows and the FP64 remainder of the MV
+// shadow (MV = MV32 + MV32lo to ~1e-15).
 __global__ void k_store_basis_vector(const double2* __restrict__ w, const double2* __restrict__ Mw,
                                      const double* __restrict__ s, double2* __restrict__ V, double2* __restrict__ MV,
-                                     float2* __restrict__ V32, float2* __restrict__ MV32, long long vstride, int j,
-                                     long long N, int P, const int* __restrict__ active) {
+                                     float2* __restrict__ V32, float2* __restrict__ MV32, float2* __restrict__ MV32lo,
+                                     long long vstride, int j, long long N, int P, const int* __restrict__ active) {
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N * P; g += (long long)gridDim.x * blockDim.x) {
     const long long p = g / N, i = g % N;
     if (active && !active[p]) continue;
@@ -506,7 +572,25 @@ __global__ void k_store_basis_vector(const double2* __restrict__ w, const double
     V[o] = a;
     MV[o] = b;
     V32[o] = make_float2((float)a.x, (float)a.y);
-    MV32[o] = make_float2((float)b.x, (float)b.y);
+    const float2 bh = make_float2((float)b.x, (float)b.y);
+    MV32[o] = bh;
+    MV32lo[o] = split_lo(b, bh);
+  }
+}
+
+// Shadows of vectors [first, first + count) of every problem (after a basis
+// rotation): V32, MV32 and MV32lo from V and MV.
+__global__ void k_refresh_shadows(const double2* __restrict__ V, const double2* __restrict__ MV,
+                                  float2* __restrict__ V32, float2* __restrict__ MV32, float2* __restrict__ MV32lo,
+                                  long long vstride, long long len, int P) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < len * P; g += (long long)gridDim.x * blockDim.x) {
+    const long long p = g / len, i = g % len;
+    const long long o = p * vstride + i;
+    const double2 a = V[o], b = MV[o];
+    V32[o] = make_float2((float)a.x, (float)a.y);
+    const float2 bh = make_float2((float)b.x, (float)b.y);
+    MV32[o] = bh;
+    MV32lo[o] = split_lo(b, bh);
   }
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -80,7 +81,7 @@ struct nfs_ctx {
   double2* MV = nullptr;
   float2* V32 = nullptr;
   float2* MV32 = nullptr;
-  float2* w32 = nullptr;
+  float2* MV32lo = nullptr;  // FP64 remainder of the MV32 shadow
   int vcap = 0;
   double* dY = nullptr;  // rotation coefficients
   size_t dY_len = 0;
@@ -88,6 +89,10 @@ struct nfs_ctx {
   long long bytes = 0;
   long long mv32 = 0, mv64 = 0;
   long long launches = 0;  // kernels this context has launched (graph nodes included)
+  double sec_cg = 0.0;     // host wall time inside the CG iteration loops
+  double sec_solve = 0.0;  // ... inside whole solves (CG + refinement residuals)
+  double sec_ritz = 0.0;   // ... in the host projected eigensolves
+  double sec_recur = 0.0, sec_orth = 0.0, sec_vec = 0.0;  // Lanczos phases
 };
 
 struct nfs_batch {
@@ -96,6 +101,10 @@ struct nfs_batch {
 };
 
 namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 thread_local char g_errbuf[256];
 
@@ -257,10 +266,6 @@ int put_flags(nfs_ctx* c, cudaStream_t s, int off, const std::vector<int>& v) {
 // --- CG ---------------------------------------------------------------------
 
 constexpr int kCgChunk = 8;
-// Lanczos vectors are kept orthogonal in the A_r inner product to within this
-// level (about sqrt of the FP64 unit round-off), which keeps the Ritz values
-// accurate to FP64 round-off (semi-orthogonality).
-constexpr double kSemiOrthogonality = 1e-8;
 
 // Enqueue kCgChunk iterations for all problems: pass 1 (which first forms
 // p = r + beta p), passes 2 and 3 (pass 3 also emits the p^* A p partials),
@@ -328,6 +333,8 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
            const std::vector<double>& tol2, int maxit, std::vector<int>& iters, std::vector<int>& status) {
   using C = nfs::cplx<R>;
   cudaStream_t s = c->work;
+  CK(cudaStreamSynchronize(s));  // earlier work is not the loop's
+  const double t0 = now_s();
   CK(cudaMemsetAsync(p, 0, c->P * c->N * sizeof(C), s));  // with beta = 0 the first pass 1 sets p = r
   nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(r, r, c->N, c->st->part_a, nfs::kStateDoubles,
                                                                    nullptr, 0);
@@ -355,6 +362,7 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
     // one product per iteration that ran (launches after convergence are empty)
     if (sizeof(R) == 4) c->mv32 += iters[q]; else c->mv64 += iters[q];
   }
+  c->sec_cg += now_s() - t0;
   return NFS_OK;
 }
 
@@ -503,19 +511,19 @@ int multi_axpy(nfs_ctx* c, double2* w, double2* Mw, int j0, int m, const std::ve
   return NFS_OK;
 }
 
-// d_p = MV32_p[0:m]^* w_p with the complex64 shadows (orthogonality monitor)
-int shadow_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, const int* d_active) {
+// d_p = MV_p[0:m]^* w_p, exact to ~1e-14 of the terms, from the split FP32
+// shadows of MV on the FP32 units (orthogonality monitor and coefficients)
+int exact_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, const int* d_active) {
   cudaStream_t s = c->work;
   const long long vstride = (long long)c->vcap * c->N;
-  nfs::k_to_c64<<<grid_blocks(c->P * c->N, 256), 256, 0, s>>>(w, c->N, c->w32, c->N, c->N, c->P);
-  constexpr int G = 8;
+  constexpr int G = 4;
   double* part = c->dscratch;
   double* fin = c->dscratch + off_fin(c);
-  nfs::k_shadow_dots<G><<<dim3(kRedBlocks, (m + G - 1) / G, c->P), kRedThreads, 0, s>>>(c->MV32, vstride, m, c->w32,
-                                                                                        c->N, part, d_active);
+  nfs::k_exact_dots<G><<<dim3(kRedBlocks, (m + G - 1) / G, c->P), kRedThreads, 0, s>>>(c->MV32, c->MV32lo, vstride, m,
+                                                                                       w, c->N, part, d_active);
   nfs::k_dots_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
   CK(cudaGetLastError());
-  c->launches += 3;
+  c->launches += 2;
   CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out.assign(c->hscratch, c->hscratch + (size_t)c->P * 2 * m);
@@ -526,29 +534,28 @@ int refresh_shadows(nfs_ctx* c, int first, int count) {
   const long long vstride = (long long)c->vcap * c->N;
   const long long len = (long long)count * c->N;
   const long long off = (long long)first * c->N;
-  const int nb = grid_blocks(len * c->P, 256);
-  nfs::k_to_c64<<<nb, 256, 0, c->work>>>(c->V + off, vstride, c->V32 + off, vstride, len, c->P);
-  nfs::k_to_c64<<<nb, 256, 0, c->work>>>(c->MV + off, vstride, c->MV32 + off, vstride, len, c->P);
+  nfs::k_refresh_shadows<<<grid_blocks(len * c->P, 256), 256, 0, c->work>>>(
+      c->V + off, c->MV + off, c->V32 + off, c->MV32 + off, c->MV32lo + off, vstride, len, c->P);
   CK(cudaGetLastError());
-  c->launches += 2;
+  c->launches += 1;
   return NFS_OK;
 }
 
 int ensure_basis(nfs_ctx* c, int m) {
   if (c->vcap >= m + 1) return NFS_OK;
-  void* olds[] = {c->V, c->MV, c->V32, c->MV32, c->w32};
+  void* olds[] = {c->V, c->MV, c->V32, c->MV32, c->MV32lo};
   for (void* p : olds)
     if (p) cudaFree(p);
-  c->bytes -= (long long)c->P * c->vcap * c->N * (16 + 16 + 8 + 8) + (c->w32 ? c->P * c->N * 8 : 0);
+  c->bytes -= (long long)c->P * c->vcap * c->N * (16 + 16 + 8 + 8 + 8);
   c->V = c->MV = nullptr;
-  c->V32 = c->MV32 = c->w32 = nullptr;
+  c->V32 = c->MV32 = c->MV32lo = nullptr;
   c->vcap = 0;
   const size_t len = (size_t)c->P * (m + 1) * c->N;
   TRY(dalloc(c, &c->V, len));
   TRY(dalloc(c, &c->MV, len));
   TRY(dalloc(c, &c->V32, len));
   TRY(dalloc(c, &c->MV32, len));
-  TRY(dalloc(c, &c->w32, (size_t)c->P * c->N));
+  TRY(dalloc(c, &c->MV32lo, len));
   c->vcap = m + 1;
   return NFS_OK;
 }
@@ -592,10 +599,10 @@ int apply_Br_basis(nfs_ctx* c, int j, double2* out) {
 // Default basis size: generous (device memory is plentiful and restarts cost
 // FP64 basis rotations), capped by half of the free device memory.
 int default_ncv(nfs_ctx* c, int nev) {
-  int m = std::max(std::max(3 * nev, 2 * nev + 2), std::min(8 * nev, 240));
+  int m = std::max(std::max(3 * nev, 2 * nev + 2), std::min(12 * nev, 320));
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-    const double per = (double)c->P * c->N * (16 + 16 + 8 + 8);
+    const double per = (double)c->P * c->N * (16 + 16 + 8 + 8 + 8);
     const int cap = (int)std::max(0.0, 0.5 * (double)fr / per) - 1;
     if (cap < m) m = std::max(cap, 2 * nev + 2);
   }
@@ -616,6 +623,8 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
   const long long vstride = (long long)c->vcap * N;
   cudaStream_t s = c->work;
   const long long mv32_0 = c->mv32, mv64_0 = c->mv64, launches_0 = c->launches;
+  const double cg_0 = c->sec_cg, solve_0 = c->sec_solve, ritz_0 = c->sec_ritz, t_begin = now_s();
+  const double recur_0 = c->sec_recur, orth_0 = c->sec_orth;
   const int nb = grid_blocks(P * N, 256);
   auto col = [&](double2* base, int p, int j) { return base + p * vstride + (long long)j * N; };
 
@@ -634,16 +643,16 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
     sc[p] = 1.0 / std::sqrt(nrm2[p]);
   }
   TRY(put_small(c, s, P, sc));
-  nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(c->t64, c->t64b, c->d_small + P, c->V, c->MV, c->V32, c->MV32, vstride,
-                                               0, N, P, nullptr);
+  nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(c->t64, c->t64b, c->d_small + P, c->V, c->MV, c->V32, c->MV32, c->MV32lo,
+                                               vstride, 0, N, P, nullptr);
   CK(cudaGetLastError());
   c->launches += 1;
 
   const int keep = std::min(m - 1, std::max(nev + 1, nev + (m - nev) / 2));
-  const int check_every = 10;
+  const int check_every = 5;
   std::vector<std::vector<double>> H(P, std::vector<double>((size_t)m * m, 0.0));
   std::vector<double> beta_last(P, 0.0);
-  std::vector<int> active(P, 1), jm(P, 0), nconv(P, 0), steps(P, 0), restarts_p(P, 0), force(P, 0);
+  std::vector<int> active(P, 1), jm(P, 0), nconv(P, 0), steps(P, 0), restarts_p(P, 0), reorths(P, 0);
   std::vector<long long> cg_total(P, 0);
   std::vector<int> status(P, NFS_OK);
   int jstart = 0, local_lo = 0, restarts = 0;
@@ -668,7 +677,11 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       // w = A_r^{-1} B_r v_j (CG); A_r w = B_r v_j
       TRY(apply_Br_basis(c, j, Mw));
       SolveOut so;
+      CK(cudaStreamSynchronize(s));
+      const double ts = now_s();
       TRY(solve(c, Mw, w, true, active, so));
+      CK(cudaStreamSynchronize(s));
+      c->sec_solve += now_s() - ts;
       for (int p = 0; p < P; ++p) {
         if (!active[p]) continue;
         if (so.status[p] == NFS_EBREAKDOWN) return NFS_EBREAKDOWN;
@@ -678,53 +691,49 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       // FP64 three-term recurrence (after a restart: the arrow of kept Ritz
       // vectors) in the A_r inner product
       const int nl = j - local_lo + 1;
+      const double tr0 = now_s();
       TRY(multi_dot(c, c->MV, local_lo, nl, w, coef, d_active));
       TRY(multi_axpy(c, w, Mw, local_lo, nl, coef, d_active));
       std::vector<double> alpha(P);
       for (int p = 0; p < P; ++p) alpha[p] = coef[(size_t)p * 2 * nl + 2 * (j - local_lo)];
       TRY(dots_re(c, s, w, Mw, bb));
-      // Partial re-orthogonalisation: measure the loss of orthogonality
-      // against the older vectors with the complex64 shadows (cheap), and
-      // re-orthogonalise exactly in FP64 against the whole basis when it
-      // exceeds the semi-orthogonality level, here and on the next step.
-      std::vector<int> reorth(P, 0);
+      const double tr1 = now_s();
+      c->sec_recur += tr1 - tr0;
+      // Partial re-orthogonalisation: every step, measure the loss of
+      // A_r-orthogonality against the older vectors [0, local_lo) with exact
+      // inner products (double-single arithmetic on the split shadows); when
+      // it exceeds orth_tol, remove those components (the vectors [local_lo,
+      // j] were just orthogonalised in FP64 by the recurrence).  The update
+      // is formed in FP32, exact enough while the coefficients are small; a
+      // large loss (a coupling after a restart) takes a second pass.
       if (local_lo > 0) {
-        TRY(shadow_dots(c, local_lo, w, d, d_active));
-        for (int p = 0; p < P; ++p) {
-          if (!active[p]) continue;
-          if (force[p]) {
-            reorth[p] = 1;
-            force[p] = 0;
-            continue;
+        std::vector<int> reorth(P, 0);
+        for (int pass = 0; pass < 3; ++pass) {
+          TRY(exact_dots(c, local_lo, w, d, d_active));
+          bool any_re = false, big = false;
+          for (int p = 0; p < P; ++p) {
+            reorth[p] = 0;
+            if (!active[p]) continue;
+            double loss = 0.0;
+            for (int i = 0; i < local_lo; ++i)
+              loss = std::max(loss, std::hypot(d[(size_t)p * 2 * local_lo + 2 * i], d[(size_t)p * 2 * local_lo + 2 * i + 1]));
+            loss /= std::sqrt(std::max(bb[p], 1e-300));
+            reorth[p] = pass == 0 ? loss > c->opt.orth_tol : loss > 1e-3 * c->opt.orth_tol + 1e-13;
+            any_re = any_re || reorth[p];
+            big = big || (reorth[p] && loss > 1e-3);
+            if (reorth[p] && pass == 0) ++reorths[p];
           }
-          double loss = 0.0;
-          for (int i = 0; i < local_lo; ++i)
-            loss = std::max(loss, std::hypot(d[(size_t)p * 2 * local_lo + 2 * i], d[(size_t)p * 2 * local_lo + 2 * i + 1]));
-          loss /= std::sqrt(std::max(bb[p], 1e-300));
-          reorth[p] = loss > kSemiOrthogonality;
-          force[p] = reorth[p];
-        }
-      } else {
-        for (int p = 0; p < P; ++p) {
-          reorth[p] = active[p] && force[p];
-          force[p] = 0;
+          if (!any_re) break;
+          TRY(put_flags(c, s, P, reorth));
+          nfs::k_shadow_axpy<<<dim3(grid_blocks(N, 256), P), 256, 0, s>>>(
+              w, Mw, c->V32, c->MV32, vstride, c->dscratch + off_fin(c), local_lo, N, c->d_flags + P);
+          CK(cudaGetLastError());
+          c->launches += 1;
+          TRY(dots_re(c, s, w, Mw, bb));
+          if (!big) break;
         }
       }
-      bool any_re = false;
-      for (int p = 0; p < P; ++p) {
-        reorth[p] = reorth[p] && active[p];
-        any_re = any_re || reorth[p];
-      }
-      if (any_re) {
-        TRY(put_flags(c, s, P, reorth));
-        for (int pass = 0; pass < 2; ++pass) {
-          TRY(multi_dot(c, c->MV, 0, j + 1, w, coef2, c->d_flags + P));
-          TRY(multi_axpy(c, w, Mw, 0, j + 1, coef2, c->d_flags + P));
-          for (int p = 0; p < P; ++p)
-            if (reorth[p]) alpha[p] += coef2[(size_t)p * 2 * (j + 1) + 2 * j];
-        }
-        TRY(dots_re(c, s, w, Mw, bb));
-      }
+      c->sec_orth += now_s() - tr1;
       for (int p = 0; p < P; ++p) {
         if (!active[p]) continue;
         if (!(bb[p] > 0)) return NFS_EBREAKDOWN;
@@ -735,8 +744,8 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
         sc[p] = 1.0 / beta;
       }
       TRY(put_small(c, s, P, sc));
-      nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(w, Mw, c->d_small + P, c->V, c->MV, c->V32, c->MV32, vstride,
-                                                   j + 1, N, P, d_active);
+      nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(w, Mw, c->d_small + P, c->V, c->MV, c->V32, c->MV32,
+                                                   c->MV32lo, vstride, j + 1, N, P, d_active);
       CK(cudaGetLastError());
       c->launches += 1;
       local_lo = j;
@@ -747,7 +756,10 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
         for (int p = 0; p < P; ++p) {
           if (!active[p]) continue;
           std::vector<double> zl;
-          if (!nfs::host::sym_eig(k, leading(p, k), theta, zl, true)) return NFS_EBREAKDOWN;
+          const double th0 = now_s();
+          const bool ok = nfs::host::sym_eig(k, leading(p, k), theta, zl, true);
+          c->sec_ritz += now_s() - th0;
+          if (!ok) return NFS_EBREAKDOWN;
           int nc = 0;
           for (int i = 0; i < nev; ++i) {
             const int cc = k - 1 - i;  // largest theta first
@@ -795,7 +807,6 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
         const double sres = beta_last[p] * zz[p][(size_t)(m - 1) * m + (m - 1 - i)];
         H[p][(size_t)keep * m + i] = H[p][(size_t)i * m + keep] = sres;
       }
-      force[p] = 1;  // the first step after a restart couples to every kept vector
       ++restarts_p[p];
     }
     TRY(refresh_shadows(c, 0, keep + 1));
@@ -804,6 +815,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
     ++restarts;
   }
   // results from each problem's leading jm x jm block: omega ascending = theta descending
+  const double tv0 = now_s();
   int worst = NFS_OK;
   std::vector<int> one(P, 0);
   for (int p = 0; p < P; ++p) {
@@ -838,6 +850,14 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       in.max_ritz_residual = maxres;
       in.status = status[p];
       in.kernel_launches = c->launches - launches_0;
+      in.seconds_total = now_s() - t_begin;
+      in.seconds_cg = c->sec_cg - cg_0;
+      in.seconds_refine = (c->sec_solve - solve_0) - (c->sec_cg - cg_0);
+      in.seconds_ritz = c->sec_ritz - ritz_0;
+      in.seconds_recurrence = c->sec_recur - recur_0;
+      in.seconds_orth = c->sec_orth - orth_0;
+      in.seconds_vectors = now_s() - tv0;
+      in.reorthogonalisations = reorths[p];
     }
     if (status[p] != NFS_OK) worst = status[p];
   }
@@ -859,7 +879,7 @@ void free_ctx(nfs_ctx* c) {
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
                   c->mat64, c->mat32, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
                   c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
-                  c->w32, c->dY};
+                  c->MV32lo, c->dY};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -882,6 +902,7 @@ struct Prepared {
 int check_options(const nfs_options& o) {
   if (o.precision != NFS_PREC_FP64 && o.precision != NFS_PREC_MIXED) return NFS_EINVAL;
   if (!(o.cg_tol > 0) || o.cg_maxit <= 0 || !(o.eig_tol > 0) || o.max_restarts < 0) return NFS_EINVAL;
+  if (!(o.orth_tol >= 0) || !(o.orth_tol < 1)) return NFS_EINVAL;
   if (o.precision == NFS_PREC_MIXED && (!(o.inner_tol > 0) || o.inner_tol >= 1 || o.max_refine <= 0))
     return NFS_EINVAL;
   if (!(o.alpha != 0.0) || !(o.beta != 0.0)) return NFS_EBASIS;
@@ -1148,6 +1169,7 @@ extern "C" void nfs_default_options(nfs_options* o) {
   o->eig_tol = 1e-10;
   o->ncv = 0;
   o->max_restarts = 200;
+  o->orth_tol = 1e-10;
   o->seed = 1;
   o->stream = nullptr;
 }

@@ -70,6 +70,7 @@ class Options(ctypes.Structure):
         ("eig_tol", ctypes.c_double),
         ("ncv", ctypes.c_int),
         ("max_restarts", ctypes.c_int),
+        ("orth_tol", ctypes.c_double),
         ("seed", ctypes.c_ulonglong),
         ("stream", ctypes.c_void_p),
     ]
@@ -106,6 +107,14 @@ class EigsInfo(ctypes.Structure):
         ("max_ritz_residual", ctypes.c_double),
         ("status", ctypes.c_int),
         ("kernel_launches", ctypes.c_longlong),
+        ("seconds_total", ctypes.c_double),
+        ("seconds_cg", ctypes.c_double),
+        ("seconds_refine", ctypes.c_double),
+        ("seconds_ritz", ctypes.c_double),
+        ("seconds_recurrence", ctypes.c_double),
+        ("seconds_orth", ctypes.c_double),
+        ("seconds_vectors", ctypes.c_double),
+        ("reorthogonalisations", ctypes.c_int),
     ]
 
 
