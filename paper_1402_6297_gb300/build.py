@@ -46,16 +46,21 @@ def up_to_date():
     return os.path.exists(lp) and os.path.getmtime(lp) >= _newest_input()
 
 
-def build(force=False, verbose=False):
-    if not force and up_to_date():
-        return lib_path()
-    os.makedirs(LIBDIR, exist_ok=True)
+def build(force=False, verbose=False, libdir=None, defines=()):
+    """Compile and link libnfs.so into libdir (default: the package's _lib).
+    defines: extra NAME=VALUE preprocessor settings (kernel tuning knobs)."""
+    out_dir = libdir or LIBDIR
+    out_lib = os.path.join(out_dir, LIBNAME)
+    if not force and not defines and libdir is None and up_to_date():
+        return out_lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = nvcc_path()
     common = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")] + ARCH
+    common += [f"-D{d}" for d in defines]
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(LIBDIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
         cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -66,13 +71,13 @@ def build(force=False, verbose=False):
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = lib_path() + ".tmp"
+    tmp = out_lib + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, lib_path())
-    return lib_path()
+    os.replace(tmp, out_lib)
+    return out_lib
 
 
 if __name__ == "__main__":

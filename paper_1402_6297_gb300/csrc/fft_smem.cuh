@@ -8,17 +8,21 @@
 // every (line, k1), a register DFT of length N2 over slots {k1 N2 + n2} and
 // writes the result to its natural position k1 + N1 k2.
 //
-// Each stage works on chunks of whole lines, one work item per thread per
-// chunk, so a thread never holds more than one item's registers.  A chunk's
-// reads and writes touch only its own lines, so the writes of chunk i and the
-// reads of chunk i + 1 share one barrier.  Work items take the line index
-// fastest across threads: with the odd-padded pitches of the callers every
-// shared-memory access of a warp is conflict-free.
+// A thread never holds more than one work item's registers.  Stage A's items
+// read and write the same slots and are disjoint, so each thread runs its
+// items one after another with a single barrier at the end.  Stage B writes
+// to other slots than it reads, so it works on chunks of whole lines: a
+// chunk's reads and writes touch only its own lines, and the writes of chunk
+// i and the reads of chunk i + 1 share one barrier.  Work items take the line
+// index fastest across threads: with the odd-padded pitches of the callers
+// every shared-memory access of a warp is conflict-free.
 //
 // tw[m] = exp(-2 pi i m / N), m < N (forward sign; the inverse conjugates).
 // Callers must __syncthreads() before; the routine ends with a barrier.
 #pragma once
 #include "fft_reg.cuh"
+
+
 
 namespace nfs {
 
@@ -56,37 +60,32 @@ __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
     __syncthreads();
   } else {
     // ---- stage A: items (line, n2) ----
+    // the items of stage A read and write the same slots and are disjoint:
+    // each thread runs its items one after another, one barrier at the end
     {
-      using CK = Chunking<N2, NLINES, NT>;
-      C ra[N1];
-      int l = 0, n2 = 0;
-      bool act = false;
+      constexpr int ITEMS = NLINES * N2;
+      constexpr int PA = (ITEMS + NT - 1) / NT;
 #pragma unroll 1
-      for (int ch = 0; ch <= CK::CHUNKS; ++ch) {
-        if (ch > 0 && act) {  // write chunk ch-1
+      for (int s = 0; s < PA; ++s) {
+        const int it = tid + s * NT;
+        if ((ITEMS % NT) == 0 || it < ITEMS) {
+          const int l = it % NLINES, n2 = it / NLINES;
           C* base = buf + l * LS + n2 * ES;
+          C ra[N1];
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1) ra[n1] = base[n1 * N2 * ES];
+          DFT<N1, INV>::run(ra);
+#pragma unroll
+          for (int k1 = 1; k1 < N1; ++k1) {
+            C w = tw[n2 * k1];
+            if (INV) w.y = -w.y;
+            ra[k1] = cmul(ra[k1], w);
+          }
 #pragma unroll
           for (int k1 = 0; k1 < N1; ++k1) base[k1 * N2 * ES] = ra[k1];
         }
-        if (ch < CK::CHUNKS) {  // read chunk ch
-          l = ch * CK::LPC + tid % CK::LPC;
-          n2 = tid / CK::LPC;
-          act = tid < CK::ITEMS && l < NLINES;
-          if (act) {
-            const C* base = buf + l * LS + n2 * ES;
-#pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) ra[n1] = base[n1 * N2 * ES];
-            DFT<N1, INV>::run(ra);
-#pragma unroll
-            for (int k1 = 1; k1 < N1; ++k1) {
-              C w = tw[n2 * k1];
-              if (INV) w.y = -w.y;
-              ra[k1] = cmul(ra[k1], w);
-            }
-          }
-        }
-        __syncthreads();
       }
+      __syncthreads();
     }
     // ---- stage B: items (line, k1) ----
     {

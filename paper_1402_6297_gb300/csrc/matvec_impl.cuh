@@ -17,10 +17,19 @@ __host__ __device__ constexpr int z_tile(int N3, int csize) {
 }
 __host__ __device__ constexpr int z_threads(int N3) { return N3 == 128 ? 512 : 384; }
 // Minimum resident CTAs per SM requested from the compiler (caps registers so
-// that two CTAs share an SM and overlap one's memory phase with the other's
-// shared-memory FFT).  Only where the shared memory also allows two.
-__host__ __device__ constexpr int plane_minb(int N, int csize) { return (csize == 8 && N >= 48 && N <= 96) ? 2 : 1; }
-__host__ __device__ constexpr int z_minb(int N3, int csize) { return (csize == 8 && N3 >= 48 && N3 <= 96) ? 2 : 1; }
+// that three CTAs share an SM and overlap one's memory phase with the others'
+// shared-memory FFTs; 96^3 complex64 planes are 75 KB, three fit in 228 KB).
+// Only for complex64 and 48 <= N <= 96, where the shared memory allows it.
+#ifndef NFS_PLANE_MINB
+#define NFS_PLANE_MINB 3
+#endif
+#ifndef NFS_Z_MINB
+#define NFS_Z_MINB 3
+#endif
+__host__ __device__ constexpr int plane_minb(int N, int csize) {
+  return (csize == 8 && N >= 48 && N <= 96) ? NFS_PLANE_MINB : 1;
+}
+__host__ __device__ constexpr int z_minb(int N3, int csize) { return (csize == 8 && N3 >= 48 && N3 <= 96) ? NFS_Z_MINB : 1; }
 
 template <typename R, int NX>
 constexpr size_t plane_smem() {

@@ -163,6 +163,30 @@ __device__ __forceinline__ int third_bound(int r) {
   return r >= 3 ? NE : ((r * NE) / 3) & ~1;
 }
 
+template <typename R>
+__device__ __forceinline__ cplx<R> pick3(int k, cplx<R> a, cplx<R> b, cplx<R> c) {
+  return k == 0 ? a : (k == 1 ? b : c);
+}
+
+// Shared-memory staging of pass 1's exchange.  Rank r computes all three
+// components of its third of the plane; its own component goes to its final
+// place, the other two to staging gaps of its plane buffer (outside its own
+// third's final positions), from which the partner CTAs load them.
+template <int NX, int NY>
+struct Stage {
+  static constexpr int PITCH = NX + 1, NE = NX * NY, TOTAL = NY * PITCH;
+  __host__ __device__ static constexpr int pos(int e) { return (e / NX) * PITCH + e % NX; }
+  __host__ __device__ static constexpr int e0(int r) { return r >= 3 ? NE : ((r * NE) / 3) & ~1; }
+  // start of the staging run of rank r's values of component r + k (k = 1, 2)
+  __host__ __device__ static constexpr int base(int r, int k) {
+    const int s = e0(r + 1) - e0(r);
+    const int lo = pos(e0(r)), hi = pos(e0(r + 1) - 1) + 1, rhi = (hi + 1) & ~1;
+    if (lo >= s && TOTAL - rhi >= s) return k == 1 ? 0 : rhi;
+    if (TOTAL - rhi >= 2 * s) return k == 1 ? rhi : rhi + s;
+    return k == 1 ? 0 : s;
+  }
+};
+
 template <typename R, int NX, int NY, int NT, int MINB>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
@@ -239,11 +263,12 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
     }
   }
   const C a3 = lam[NX + NY + i3];
-  C* dst0 = cl.map_shared_rank(plane, 0);
-  C* dst1 = cl.map_shared_rank(plane, 1);
-  C* dst2 = cl.map_shared_rank(plane, 2);
-  cl.sync();  // every CTA of the cluster is resident before remote stores
-
+  // exchange through shared memory: all three components of this third are
+  // computed here; this rank's goes to its final place, the other two to
+  // staging runs that the partner CTAs load after the cluster barrier
+  using SG = Stage<NX, NY>;
+  const int sb1 = SG::base(rank, 1), sb2 = SG::base(rank, 2);
+  const int r1 = rank == 2 ? 0 : rank + 1, r2 = rank == 0 ? 2 : rank - 1;
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
     const int v = b * NT + (int)threadIdx.x;
@@ -251,8 +276,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
 #pragma unroll
       for (int h = 0; h < EPV; ++h) {
         const int e = e0 + v * EPV + h;
-        C va, vb;
-        if constexpr (EPV == 2) {
+        C va, vb;        if constexpr (EPV == 2) {
           va = h == 0 ? mk(ra[b].x, ra[b].y) : mk(ra[b].z, ra[b].w);
           vb = h == 0 ? mk(rb[b].x, rb[b].y) : mk(rb[b].z, rb[b].w);
         } else {
@@ -273,13 +297,58 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
           for (int k = 0; k < 3; ++k) o[k] = cadd(cmulc(B.x[k], va), cmulc(B.c[k], vb));
         }
         const int sidx = i2 * PITCH + i1;
-        dst0[sidx] = o[0];
-        dst1[sidx] = o[1];
-        dst2[sidx] = o[2];
+        plane[sidx] = pick3<R>(rank, o[0], o[1], o[2]);
+        plane[sb1 + (e - e0)] = pick3<R>(r1, o[0], o[1], o[2]);
+        plane[sb2 + (e - e0)] = pick3<R>(r2, o[0], o[1], o[2]);
       }
     }
   }
-  cl.sync();
+  cl.sync();  // staging complete in every CTA of the cluster
+  {
+    // load this rank's component of the two other thirds from the partners'
+    // staging runs, then (after every CTA has read) put them in place
+    using V = typename Vec16<C>::type;
+    constexpr int S_MAX = (NE / 3 + 2) / EPV;
+    constexpr int PER2 = (S_MAX + NT - 1) / NT;
+    V g[2][PER2];
+    int gt[2], gn[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int t = q == 0 ? r1 : r2;               // partner rank (its third)
+      const int k = q == 0 ? 2 : 1;                 // this rank = t + k (mod 3)
+      const V* src = reinterpret_cast<const V*>(cl.map_shared_rank(plane, t) + SG::base(t, k));
+      gt[q] = t;
+      gn[q] = (SG::e0(t + 1) - SG::e0(t)) / EPV;
+#pragma unroll
+      for (int b = 0; b < PER2; ++b) {
+        const int v = b * NT + (int)threadIdx.x;
+        if (v < gn[q]) g[q][b] = src[v];
+      }
+    }
+    cl.sync();  // every CTA has read its partners' staging
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int te0 = SG::e0(gt[q]);
+#pragma unroll
+      for (int b = 0; b < PER2; ++b) {
+        const int v = b * NT + (int)threadIdx.x;
+        if (v < gn[q]) {
+#pragma unroll
+          for (int h = 0; h < EPV; ++h) {
+            const int e = te0 + v * EPV + h;
+            C val;
+            if constexpr (EPV == 2) {
+              val = h == 0 ? mk(g[q][b].x, g[q][b].y) : mk(g[q][b].z, g[q][b].w);
+            } else {
+              val = g[q][b];
+            }
+            plane[(e / NX) * PITCH + (e % NX)] = val;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
   smem_fft<true, NX, NY, NT, PITCH, 1>(plane, stx);  // along x (rows)
   smem_fft<true, NY, NX, NT, 1, PITCH>(plane, sty);  // along y (columns)
   C* out = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
@@ -290,10 +359,6 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
 // pass 2: the material product of eq. factor_mtx, per real-space voxel:
 //   w = Phi^{-1} (xi mu^{-1} p + q),   f = mu^{-1} (zeta w + p)
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ cplx<R> pick3(int k, cplx<R> a, cplx<R> b, cplx<R> c) {
-  return k == 0 ? a : (k == 1 ? b : c);
-}
 
 template <typename R>
 __device__ __forceinline__ void material_apply(const MatView<R>& m, long long v, const cplx<R>* p,
