@@ -10,6 +10,7 @@
 // (or for problems already converged) cost only empty launches.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "nfs_complex.cuh"
 
@@ -17,7 +18,9 @@ namespace nfs {
 
 constexpr int kRedBlocks = 304;   // two blocks per SM on a 152-SM GB300
 constexpr int kRedThreads = 256;
-constexpr int kMaxPartials = 1024;  // >= 6 * n3 (pass-3 CTAs) and kRedBlocks
+constexpr int kMaxPartials = 1024;  // >= 6 * n3 (pass-3 CTAs), kRedBlocks and kUpdBlocks
+constexpr int kUpdBlocks = 608;     // x/r update grid: four blocks of 512 per SM
+constexpr int kUpdThreads = 512;
 
 // CG scalar state of one problem, device resident (an array of P).
 struct CGState {
@@ -29,7 +32,7 @@ struct CGState {
   int done;         // 1: converged, broken down or out of iterations
   int status;       // 0, -6 (no convergence) or -7 (breakdown)
   int npart_a;      // number of valid entries of part_a
-  int pad_;
+  unsigned int arrived;  // blocks of the x/r update that have written their partial
   double part_a[kMaxPartials];  // partials of p^* A p (written by pass 3 or k_dot_re)
   double part_b[kMaxPartials];  // partials of r^* r
 };
@@ -125,29 +128,41 @@ k_cg_init(CGState* st, const double* __restrict__ tol2, int maxit, int npart_a) 
     st->maxit = maxit;
     st->status = 0;
     st->alpha = st->beta = 0.0;
+    st->arrived = 0;
     st->done = (rr <= t2) ? 1 : 0;
     if (!(rr == rr)) { st->done = 1; st->status = -7; }
   }
 }
 
-// alpha = rr / p^*Ap (every block sums the npart_a partials in the same
-// order, so all blocks agree; block 0 records it), then
-// x += alpha p ; r -= alpha Ap ; part_b[block] = partial r^* r.  Grid (kRedBlocks, P).
+// One CG step after the product, for every problem (grid (kUpdBlocks, P)):
+// alpha = rr / p^*Ap (every block sums the npart_a partials of p^* A p in the
+// same order, so all blocks agree; block 0 records it), x += alpha p,
+// r -= alpha Ap, and block b's partial of the new r^* r.  The last block to
+// finish (counted with an atomic, no waiting) sums the partials in fixed
+// order and sets beta = rr_new / rr, the convergence flag and the iteration
+// count for the next launch.  Vectors move in 16-byte loads.
 template <typename C>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kUpdThreads)
 k_cg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __restrict__ p, const C* __restrict__ Ap, long long N,
                CGState* st) {
   const int pb = blockIdx.y;
   st += pb;
   if (st->done) return;
-  x += (long long)pb * N;
-  r += (long long)pb * N;
-  p += (long long)pb * N;
-  Ap += (long long)pb * N;
+  using V = typename std::conditional<sizeof(C) == 8, float4, double2>::type;
+  constexpr int EPV = 16 / (int)sizeof(C);
+  V* x4 = reinterpret_cast<V*>(x + (long long)pb * N);
+  V* r4 = reinterpret_cast<V*>(r + (long long)pb * N);
+  const V* p4 = reinterpret_cast<const V*>(p + (long long)pb * N);
+  const V* a4 = reinterpret_cast<const V*>(Ap + (long long)pb * N);
   using R = typename RealOf<C>::type;
   __shared__ double s_alpha;
-  __shared__ int s_ok;
-  const double pAp = sum_partials(st->part_a, st->npart_a);  // valid in thread 0 only
+  __shared__ int s_ok, s_last;
+  double pAp;
+  {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < st->npart_a; i += kUpdThreads) v += st->part_a[i];
+    pAp = block_sum<kUpdThreads>(v);  // valid in thread 0
+  }
   if (threadIdx.x == 0) {
     s_alpha = st->rr / pAp;
     s_ok = (pAp > 0.0) && (s_alpha == s_alpha);  // also catches NaN
@@ -164,27 +179,38 @@ k_cg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __restrict__ p, co
   if (!s_ok) return;  // breakdown: leave x, r untouched (uniform per block)
   const R al = (R)s_alpha;
   Acc<C> acc;
-  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
-    const C pi = p[i], api = Ap[i];
-    C xi = x[i], ri = r[i];
-    xi.x += al * pi.x;
-    xi.y += al * pi.y;
-    ri.x -= al * api.x;
-    ri.y -= al * api.y;
-    x[i] = xi;
-    r[i] = ri;
-    acc.add(ri.x * ri.x + ri.y * ri.y);
+  const long long NV = N / EPV;
+  for (long long i = (long long)blockIdx.x * kUpdThreads + threadIdx.x; i < NV;
+       i += (long long)gridDim.x * kUpdThreads) {
+    const V pi = p4[i], ai = a4[i];
+    V xi = x4[i], ri = r4[i];
+    if constexpr (EPV == 2) {
+      xi.x += al * pi.x; xi.y += al * pi.y; xi.z += al * pi.z; xi.w += al * pi.w;
+      ri.x -= al * ai.x; ri.y -= al * ai.y; ri.z -= al * ai.z; ri.w -= al * ai.w;
+      acc.add(ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w);
+    } else {
+      xi.x += al * pi.x; xi.y += al * pi.y;
+      ri.x -= al * ai.x; ri.y -= al * ai.y;
+      acc.add(ri.x * ri.x + ri.y * ri.y);
+    }
+    x4[i] = xi;
+    r4[i] = ri;
   }
-  const double s = block_sum<kRedThreads>(acc.total());
-  if (threadIdx.x == 0) st->part_b[blockIdx.x] = s;
-}
-
-// One block per problem: new residual norm, convergence, beta.
-__global__ void __launch_bounds__(kRedThreads) k_cg_beta(CGState* st) {
-  st += blockIdx.x;
-  if (st->done) return;
-  const double rr = sum_partials(st->part_b);
+  const double s = block_sum<kUpdThreads>(acc.total());
   if (threadIdx.x == 0) {
+    st->part_b[blockIdx.x] = s;
+    __threadfence();
+    s_last = atomicAdd(&st->arrived, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // the last block: new residual norm, convergence, beta
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += kUpdThreads) v += ((volatile double*)st->part_b)[i];
+  const double rr = block_sum<kUpdThreads>(v);
+  if (threadIdx.x == 0) {
+    st->arrived = 0;
     st->it += 1;
     if (!(rr == rr)) {
       st->status = -7;

@@ -268,8 +268,8 @@ int put_flags(nfs_ctx* c, cudaStream_t s, int off, const std::vector<int>& v) {
 constexpr int kCgChunk = 8;
 
 // Enqueue kCgChunk iterations for all problems: pass 1 (which first forms
-// p = r + beta p), passes 2 and 3 (pass 3 also emits the p^* A p partials),
-// the x/r update (which forms alpha itself) and the beta kernel.
+// p = r + beta p), passes 2 and 3 (pass 3 also emits the p^* A p partials)
+// and the x/r update (which forms alpha, and in its last block beta).
 template <typename R>
 cudaError_t enqueue_cg_chunk(nfs_ctx* c, cudaStream_t s, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p,
                              nfs::cplx<R>* Ap) {
@@ -282,8 +282,7 @@ cudaError_t enqueue_cg_chunk(nfs_ctx* c, cudaStream_t s, nfs::cplx<R>* x, nfs::c
   for (int i = 0; i < kCgChunk; ++i) {
     cudaError_t e = nfs::matvec_launch<R>(a);
     if (e != cudaSuccess) return e;
-    nfs::k_cg_update_xr<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(x, r, p, Ap, c->N, c->st);
-    nfs::k_cg_beta<<<c->P, kRedThreads, 0, s>>>(c->st);
+    nfs::k_cg_update_xr<C><<<dim3(nfs::kUpdBlocks, c->P), nfs::kUpdThreads, 0, s>>>(x, r, p, Ap, c->N, c->st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -292,7 +291,7 @@ cudaError_t enqueue_cg_chunk(nfs_ctx* c, cudaStream_t s, nfs::cplx<R>* x, nfs::c
 
 // The chunk as a CUDA graph, captured once per (precision, buffers) on the
 // context's work stream and replayed: one launch per chunk instead of
-// 5 kCgChunk kernel launches.
+// 4 kCgChunk kernel launches.
 template <typename R>
 int cg_chunk_graph(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::cplx<R>* Ap,
                    cudaGraphExec_t* out) {
@@ -347,7 +346,7 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
   const size_t head = offsetof(CGState, part_a);
   for (;;) {
     CK(cudaGraphLaunch(exec, s));
-    c->launches += 5 * kCgChunk;
+    c->launches += 4 * kCgChunk;
     CK(cudaMemcpy2DAsync(c->st_host, sizeof(CGState), c->st, sizeof(CGState), head, c->P, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     bool all = true;
