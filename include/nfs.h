@@ -83,7 +83,9 @@ typedef struct {
   double alpha, beta;      /* free parameters of Lambda_p (eq. mtx_Lambda_p_q)    */
   double cg_tol;           /* relative residual ||b - A_r x|| / ||b|| to reach    */
   int cg_maxit;            /* CG iteration cap (per refinement step when mixed)   */
-  double inner_tol;        /* mixed: residual reduction of each FP32 inner solve  */
+  double inner_tol;        /* mixed: residual reduction of each FP32 inner solve
+                            * (looser when the remaining reduction to cg_tol is
+                            * smaller)                                          */
   int max_refine;          /* mixed: cap on FP64 refinement steps                 */
   double eig_tol;          /* Lanczos: Ritz residual <= eig_tol * |theta|         */
   int ncv;                 /* Lanczos basis size; 0 means max(3 nev, 2 nev + 2)   */
@@ -129,8 +131,8 @@ typedef struct {
 } nfs_eigs_info;
 
 /* Defaults: FP64, alpha = 2, beta = 3, cg_tol 1e-12, cg_maxit 2000,
- * inner_tol 1e-5, max_refine 8, eig_tol 1e-10, ncv 0, max_restarts 200,
- * seed 1, default stream. */
+ * inner_tol 1e-6, max_refine 8, eig_tol 1e-10, ncv 0, max_restarts 200,
+ * orth_tol 1e-10, seed 1, default stream. */
 void nfs_default_options(nfs_options* opt);
 
 /* Build a context for one Bloch problem (Algorithm alg:NullSpaceFree, steps

@@ -236,6 +236,29 @@ __global__ void k_sub(const C* __restrict__ a, const C* __restrict__ b, C* __res
     y[i] = csub(a[i], b[i]);
 }
 
+// Refinement residual per problem p (skip64, skip32: the masks of the two
+// products just launched): r_p = b_p - Ap64_p where the complex128 product ran
+// (!skip64[p]), else r_p -= s_p Ap32_p where the complex64 product of the
+// correction ran (!skip32[p]), else r_p is left.  Grid-stride over P x N.
+__global__ void k_refine_residual(double2* __restrict__ r, const double2* __restrict__ b,
+                                  const double2* __restrict__ Ap64, const float2* __restrict__ Ap32,
+                                  const double* __restrict__ s, const int* __restrict__ skip64,
+                                  const int* __restrict__ skip32, long long N, long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / N;
+    if (!skip64[p]) {
+      r[i] = csub(b[i], Ap64[i]);
+    } else if (!skip32[p]) {
+      const float2 a = Ap32[i];
+      const double f = s[p];
+      double2 ri = r[i];
+      ri.x -= f * (double)a.x;
+      ri.y -= f * (double)a.y;
+      r[i] = ri;
+    }
+  }
+}
+
 // complex64 <- complex128 * s[problem]
 __global__ void k_demote(const double2* __restrict__ a, const double* __restrict__ s, float2* __restrict__ y,
                          long long N, long long total) {

@@ -246,9 +246,10 @@ int dots_re(nfs_ctx* c, cudaStream_t s, const C* x, const C* y, std::vector<doub
 }
 
 // Layout of d_small (doubles): [0, P) tolerances, [P, 2P) and [2P, 3P) scales;
-// of d_flags (ints): [0, P) active problems, [P, 2P) a second mask.
+// of d_flags (ints): [0, P) active problems, [P, 2P) a second mask, [2P, 4P)
+// the skip masks of the two refinement products.
 constexpr int kSmallSlots = 3;
-constexpr int kFlagSlots = 2;
+constexpr int kFlagSlots = 4;
 
 // upload v to c->d_small + off through the pinned mirror
 int put_small(nfs_ctx* c, cudaStream_t s, int off, const std::vector<double>& v) {
@@ -415,15 +416,23 @@ int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, const std::vect
     }
     return NFS_OK;
   }
-  // mixed precision
+  // mixed precision.  Round k: d = A32^{-1} (r_k / |r_k|) by complex64 CG,
+  // x += |r_k| d, then the next residual.  While the correction is of the
+  // size of x (|r_k| large) the residual needs the complex128 product,
+  // r = b - A x.  Once |r_k| <= kCheapRefine * tol * |b| it is updated as
+  // r -= |r_k| A32 d with the complex64 product of the correction: that
+  // product's relative error (~5e-7) then moves r by at most ~1% of the
+  // tolerance.  The inner tolerance is inner_tol, or looser where the
+  // remaining reduction tol |b| / |r_k| asks for less.
+  constexpr double kCheapRefine = 2.5e4;
   const int nb = grid_blocks(tot, 256);
   std::vector<double> rr;
   std::vector<int> live(need);
   for (;;) {
     TRY(dots_re(c, s, c->r64, c->r64, rr));
-    bool any = false;
+    bool any = false, any64 = false, any32 = false;
     std::vector<double> inv(P, 0.0), nrm(P, 0.0), itol2(P, INFINITY);
-    std::vector<int> skip(P, 1);
+    std::vector<int> skip(P, 1), skip64(P, 1), skip32(P, 1);
     for (int q = 0; q < P; ++q) {
       if (!live[q]) continue;
       so.relres[q] = std::sqrt(std::max(rr[q], 0.0) / bb[q]);
@@ -433,8 +442,17 @@ int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, const std::vect
       any = true;
       nrm[q] = std::sqrt(rr[q]);
       inv[q] = 1.0 / nrm[q];
-      itol2[q] = c->opt.inner_tol * c->opt.inner_tol;
+      const double need_red = 0.3 * tol * std::sqrt(bb[q]) / nrm[q];
+      const double itol = std::max(c->opt.inner_tol, std::min(need_red, 0.1));
+      itol2[q] = itol * itol;
       skip[q] = 0;
+      if (nrm[q] <= kCheapRefine * tol * std::sqrt(bb[q])) {
+        skip32[q] = 0;
+        any32 = true;
+      } else {
+        skip64[q] = 0;
+        any64 = true;
+      }
     }
     if (!any) break;
     TRY(put_small(c, s, P, inv));
@@ -448,10 +466,15 @@ int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, const std::vect
     nfs::k_axpy_promote<<<nb, 256, 0, s>>>(x, c->d_small + 2 * P, c->x32, c->N, tot);
     CK(cudaGetLastError());
     c->launches += 1;
-    // refinement residual with the complex128 product, skipping finished problems
-    TRY(put_flags(c, s, P, skip));
-    TRY(matvec<double>(c, s, x, c->Ap64, c->d_flags + P, 1));
-    TRY(sub64(c, s, b, c->Ap64, c->r64));
+    // next residual: complex128 product of x, or complex64 product of d
+    TRY(put_flags(c, s, 2 * P, skip64));
+    TRY(put_flags(c, s, 3 * P, skip32));
+    if (any64) TRY(matvec<double>(c, s, x, c->Ap64, c->d_flags + 2 * P, 1));
+    if (any32) TRY(matvec<float>(c, s, c->x32, c->Ap32, c->d_flags + 3 * P, 1));
+    nfs::k_refine_residual<<<nb, 256, 0, s>>>(c->r64, b, c->Ap64, c->Ap32, c->d_small + 2 * P, c->d_flags + 2 * P,
+                                              c->d_flags + 3 * P, c->N, tot);
+    CK(cudaGetLastError());
+    c->launches += 1;
     for (int q = 0; q < P; ++q) {
       if (skip[q]) continue;
       so.iters[q] += it[q];
@@ -1163,7 +1186,7 @@ extern "C" void nfs_default_options(nfs_options* o) {
   o->beta = 3.0;
   o->cg_tol = 1e-12;
   o->cg_maxit = 2000;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-6;
   o->max_refine = 8;
   o->eig_tol = 1e-10;
   o->ncv = 0;

@@ -116,6 +116,24 @@ def test_cg_solve(nfs, precision):
     ctx.close()
 
 
+def test_mixed_refinement_reports_true_residual(nfs):
+    """Mixed refinement switches to the complex64 product of the correction
+    once the residual is small; the residual it then reports (a recursive one)
+    must stay within a few percent of the tolerance of the true residual."""
+    g = (48, 48, 48)
+    med = wl.pseudochiral_cylinders(g, 4, 0.1, 13.0, 1.0, 0.4, (0, 1), seed=1)
+    tol = 1e-10
+    ctx = nfs.Context(g, K, med, precision="mixed", cg_tol=tol)
+    orc = nfgep.NFGEP(g, K, med)
+    b = wl.random_complex(4 * ctx.n, 12)
+    x, info = ctx.cg_solve(torch.from_numpy(b).cuda())
+    assert info.status == 0 and info.refinements >= 2
+    res = np.linalg.norm(orc.Ar(x.cpu().numpy()) - b) / np.linalg.norm(b)
+    assert res <= 1.05 * tol, res
+    assert abs(res - info.rel_residual) <= 0.05 * tol, (res, info.rel_residual)
+    ctx.close()
+
+
 def test_cg_nonzero_initial_guess_and_maxit(nfs):
     g = (12, 12, 12)
     med = wl.chiral_sphere(g)
