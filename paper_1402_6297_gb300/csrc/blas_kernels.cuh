@@ -467,11 +467,16 @@ __global__ void k_shadow_axpy(double2* __restrict__ w, double2* __restrict__ Mw,
   V32 += (long long)p * vstride;
   MV32 += (long long)p * vstride;
   d += (long long)p * m * 2;
+  // the coefficients as floats, converted once per block (double-precision
+  // conversions run at the FP64 rate)
+  extern __shared__ float2 sd[];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) sd[j] = make_float2((float)d[2 * j], (float)d[2 * j + 1]);
+  __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int j = 0; j < m; ++j) {
-      const float2 cj = make_float2((float)d[2 * j], (float)d[2 * j + 1]);
+      const float2 cj = sd[j];
       const float2 v = V32[(long long)j * N + i], mv = MV32[(long long)j * N + i];
       a = cadd(a, cmul(cj, v));
       b = cadd(b, cmul(cj, mv));
@@ -544,26 +549,26 @@ k_dots_finish(const double* __restrict__ part, int m, int nb, double* __restrict
 }
 
 // part[(((p * m + j) * gridDim.x) + b) * 2 + {0, 1}] = block b's share of
-// conj(S_pj)^T w_p (S = Shi + Slo) for the G vectors j = blockIdx.y * G + g < m;
-// grid (kRedBlocks, ceil(m / G), P).  w is FP64 and split here.
+// conj(S_pj)^T w_p (S = Shi + Slo, w = whi + wlo) for the G vectors
+// j = blockIdx.y * G + g < m; grid (kRedBlocks, ceil(m / G), P).
 template <int G>
 __global__ void __launch_bounds__(kRedThreads)
 k_exact_dots(const float2* __restrict__ Shi, const float2* __restrict__ Slo, long long sstride, int m,
-             const double2* __restrict__ w, long long N, double* __restrict__ part, const int* __restrict__ active) {
+             const float2* __restrict__ whi, const float2* __restrict__ wlo, long long N, double* __restrict__ part,
+             const int* __restrict__ active) {
   const int p = blockIdx.z;
   if (active && !active[p]) return;
   Shi += (long long)p * sstride;
   Slo += (long long)p * sstride;
-  w += (long long)p * N;
+  whi += (long long)p * N;
+  wlo += (long long)p * N;
   const int j0 = blockIdx.y * G;
   DSAcc re[G], im[G];
   float sre[G], sim[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) sre[g] = sim[g] = 0.f;
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
-    const double2 wd = w[i];
-    const float2 bh = make_float2((float)wd.x, (float)wd.y);
-    const float2 bl = split_lo(wd, bh);
+    const float2 bh = whi[i], bl = wlo[i];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (j0 + g < m) {
@@ -602,6 +607,18 @@ k_exact_dots(const float2* __restrict__ Shi, const float2* __restrict__ Slo, lon
       part[o] = sr;
       part[o + 1] = si;
     }
+  }
+}
+
+// w -> (whi, wlo) floats with whi + wlo = w to ~1e-15 (once per vector, so
+// that the inner-product kernel runs no double-precision arithmetic)
+__global__ void k_split_hi_lo(const double2* __restrict__ w, float2* __restrict__ whi, float2* __restrict__ wlo,
+                              long long total) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = w[i];
+    const float2 h = make_float2((float)v.x, (float)v.y);
+    whi[i] = h;
+    wlo[i] = split_lo(v, h);
   }
 }
 

@@ -29,6 +29,8 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "fft_smem.cuh"
 #include "matvec.h"
 
@@ -57,14 +59,29 @@ template <typename C> struct Vec16;
 template <> struct Vec16<float2> { using type = float4; };
 template <> struct Vec16<double2> { using type = double2; };
 
-// Bursts of 16-byte global loads: thread t handles vectors t, t + NT, ...
-// (NV vectors in all), issued BATCH at a time before any is consumed, so
-// that every thread keeps BATCH requests in flight.  put(element_index, value)
-// receives each complex element.
+// How the passes move elements between global and shared memory: EPV
+// consecutive elements per lane in one vector V.  One element per lane
+// (8-byte accesses for complex64, still 256 contiguous bytes per warp) keeps
+// every shared-memory access of a warp on consecutive addresses, free of bank
+// conflicts; pairs (16-byte accesses) halve the instruction count but make
+// 8-byte shared accesses stride 16 bytes, a two-way conflict.
+#ifndef NFS_C64_PAIRS
+#define NFS_C64_PAIRS 0
+#endif
+template <typename C>
+struct Lane {
+  static constexpr int EPV = (sizeof(C) == 8 && NFS_C64_PAIRS) ? 2 : 1;
+  using V = typename std::conditional<EPV == 2, float4, C>::type;
+};
+
+// Bursts of global loads of Lane<C> vectors: thread t handles vectors t,
+// t + NT, ... (NV vectors in all), issued BATCH at a time before any is
+// consumed, so that every thread keeps BATCH requests in flight.
+// put(element_index, value) receives each complex element.
 template <int NV, int NT, int BATCH, typename C, typename Put>
 __device__ __forceinline__ void burst_load(const C* __restrict__ src, Put put) {
-  using V = typename Vec16<C>::type;
-  constexpr int EPV = 16 / (int)sizeof(C);
+  using V = typename Lane<C>::V;
+  constexpr int EPV = Lane<C>::EPV;
   constexpr int PER = (NV + NT - 1) / NT;
   const V* s = reinterpret_cast<const V*>(src);
 #pragma unroll
@@ -90,12 +107,11 @@ __device__ __forceinline__ void burst_load(const C* __restrict__ src, Put put) {
   }
 }
 
-// 16-byte stores: element pairs (complex64) or single elements (complex128)
-// taken from get(element_index).
+// Global stores of Lane<C> vectors taken from get(element_index).
 template <int NV, int NT, typename C, typename Get>
 __device__ __forceinline__ void burst_store(C* __restrict__ dst, Get get) {
-  using V = typename Vec16<C>::type;
-  constexpr int EPV = 16 / (int)sizeof(C);
+  using V = typename Lane<C>::V;
+  constexpr int EPV = Lane<C>::EPV;
   V* d = reinterpret_cast<V*>(dst);
   for (int v = (int)threadIdx.x; v < NV; v += NT) {
     if constexpr (EPV == 2) {
@@ -197,7 +213,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
-  constexpr int EPV = 16 / (int)sizeof(C);
+  constexpr int EPV = Lane<C>::EPV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* plane = reinterpret_cast<C*>(smem_raw);
   C* stx = plane + NY * PITCH;
@@ -222,9 +238,8 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
   const int e0 = third_bound<NE>(rank), e1 = third_bound<NE>(rank + 1);
   const C* ua = u + (2 * grp) * n + (long long)i3 * NE + e0;
   const C* ub = ua + n;
-  // this rank's inputs, loaded with 16-byte bursts into registers (both
-  // halves in flight together)
-  using V = typename Vec16<C>::type;
+  // this rank's inputs, loaded into registers (both halves in flight together)
+  using V = typename Lane<C>::V;
   constexpr int NVMAX = (NE / 3 + 2) / EPV;
   constexpr int PER = (NVMAX + NT - 1) / NT;
   const int nv = (e1 - e0) / EPV;
@@ -276,7 +291,8 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
 #pragma unroll
       for (int h = 0; h < EPV; ++h) {
         const int e = e0 + v * EPV + h;
-        C va, vb;        if constexpr (EPV == 2) {
+        C va, vb;
+        if constexpr (EPV == 2) {
           va = h == 0 ? mk(ra[b].x, ra[b].y) : mk(ra[b].z, ra[b].w);
           vb = h == 0 ? mk(rb[b].x, rb[b].y) : mk(rb[b].z, rb[b].w);
         } else {
@@ -307,7 +323,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
   {
     // load this rank's component of the two other thirds from the partners'
     // staging runs, then (after every CTA has read) put them in place
-    using V = typename Vec16<C>::type;
+    using V = typename Lane<C>::V;
     constexpr int S_MAX = (NE / 3 + 2) / EPV;
     constexpr int PER2 = (S_MAX + NT - 1) / NT;
     V g[2][PER2];
@@ -416,8 +432,8 @@ __global__ void __launch_bounds__(NT, MINB)
 k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __restrict__ twz, int ncols,
                    R inv_n, const int* __restrict__ skip, BatchStrides bs) {
   using C = cplx<R>;
-  using V = typename Vec16<C>::type;
-  constexpr int EPV = 16 / (int)sizeof(C);
+  using V = typename Lane<C>::V;
+  constexpr int EPV = Lane<C>::EPV;
   constexpr int LINES = 6 * TX;
   constexpr int PITCH = LINES + 1;
   constexpr int VPR = TX / EPV;             // 16-byte vectors per (field, z) run
@@ -508,7 +524,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
-  constexpr int EPV = 16 / (int)sizeof(C);
+  constexpr int EPV = Lane<C>::EPV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* plane = reinterpret_cast<C*>(smem_raw);
   C* stx = plane + NY * PITCH;
@@ -545,12 +561,17 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   const C a3 = lam[NX + NY + i3];
   const int e0 = third_bound<NE>(rank), e1 = third_bound<NE>(rank + 1);
   double dot_acc = 0.0;
-  // element pairs (i1 even) so that the two outputs leave as 16-byte stores
-  for (int ep = e0 / 2 + threadIdx.x; ep < e1 / 2; ep += NT) {
-    C r0[2], r1[2];
+  using V = typename Lane<C>::V;
+  V* o0v = reinterpret_cast<V*>(o0);
+  V* o1v = reinterpret_cast<V*>(o1);
+  const C* u0 = u + (2 * grp) * n + (long long)i3 * NE;
+  const C* u1 = u0 + n;
+  // EPV consecutive elements per lane (e0, e1 even)
+  for (int ev = e0 / EPV + (int)threadIdx.x; ev < e1 / EPV; ev += NT) {
+    C r0[EPV], r1[EPV];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int e = 2 * ep + h;
+    for (int h = 0; h < EPV; ++h) {
+      const int e = ev * EPV + h;
       const int i1 = e % NX, i2 = e / NX;
       const int s = i2 * PITCH + i1;
       const C f[3] = {src0[s], src1[s], src2[s]};
@@ -567,25 +588,21 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
       }
     }
     if constexpr (EPV == 2) {
-      reinterpret_cast<float4*>(o0)[ep] = make_float4(r0[0].x, r0[0].y, r0[1].x, r0[1].y);
-      reinterpret_cast<float4*>(o1)[ep] = make_float4(r1[0].x, r1[0].y, r1[1].x, r1[1].y);
+      o0v[ev] = make_float4(r0[0].x, r0[0].y, r0[1].x, r0[1].y);
+      o1v[ev] = make_float4(r1[0].x, r1[0].y, r1[1].x, r1[1].y);
     } else {
-      o0[2 * ep] = r0[0];
-      o0[2 * ep + 1] = r0[1];
-      o1[2 * ep] = r1[0];
-      o1[2 * ep + 1] = r1[1];
+      o0v[ev] = r0[0];
+      o1v[ev] = r1[0];
     }
     if (dot_part != nullptr) {
       // Re(u^* A u) over this CTA's outputs (the CG curvature p^* A p)
-      const C* u0 = u + (2 * grp) * n + (long long)i3 * NE;
-      const C* u1 = u0 + n;
-      R s = 0;
+      R sacc = 0;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const C pa = u0[2 * ep + h], pb = u1[2 * ep + h];
-        s += pa.x * r0[h].x + pa.y * r0[h].y + pb.x * r1[h].x + pb.y * r1[h].y;
+      for (int h = 0; h < EPV; ++h) {
+        const C pa = u0[ev * EPV + h], pb = u1[ev * EPV + h];
+        sacc += pa.x * r0[h].x + pa.y * r0[h].y + pb.x * r1[h].x + pb.y * r1[h].y;
       }
-      dot_acc += (double)s;
+      dot_acc += (double)sacc;
     }
   }
   if (dot_part != nullptr) {

@@ -541,11 +541,15 @@ int exact_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, co
   constexpr int G = 4;
   double* part = c->dscratch;
   double* fin = c->dscratch + off_fin(c);
+  // w split once into floats (the CG work vectors x32 / r32 are free here)
+  float2* whi = c->x32 ? c->x32 : reinterpret_cast<float2*>(c->Ap64);
+  float2* wlo = c->x32 ? c->r32 : reinterpret_cast<float2*>(c->Ap64) + c->P * c->N;
+  nfs::k_split_hi_lo<<<grid_blocks(c->P * c->N, 256), 256, 0, s>>>(w, whi, wlo, c->P * c->N);
   nfs::k_exact_dots<G><<<dim3(kRedBlocks, (m + G - 1) / G, c->P), kRedThreads, 0, s>>>(c->MV32, c->MV32lo, vstride, m,
-                                                                                       w, c->N, part, d_active);
+                                                                                       whi, wlo, c->N, part, d_active);
   nfs::k_dots_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
   CK(cudaGetLastError());
-  c->launches += 2;
+  c->launches += 3;
   CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out.assign(c->hscratch, c->hscratch + (size_t)c->P * 2 * m);
@@ -747,7 +751,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
           }
           if (!any_re) break;
           TRY(put_flags(c, s, P, reorth));
-          nfs::k_shadow_axpy<<<dim3(grid_blocks(N, 256), P), 256, 0, s>>>(
+          nfs::k_shadow_axpy<<<dim3(grid_blocks(N, 256), P), 256, (size_t)local_lo * sizeof(float2), s>>>(
               w, Mw, c->V32, c->MV32, vstride, c->dscratch + off_fin(c), local_lo, N, c->d_flags + P);
           CK(cudaGetLastError());
           c->launches += 1;
