@@ -35,14 +35,22 @@ struct Chunking {
   static constexpr int ITEMS = LPC * ITEMS_PER_LINE;  // work items per chunk (<= NT when LPC0 >= 1)
 };
 
-template <bool INV, int N, int NLINES, int NT, int LS, int ES, typename C>
-__device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
+// The line DFTs with optional global-memory ends: with IN_GLOBAL the first
+// stage reads element e of line l as get(l, e) (natural order) instead of
+// from buf; with OUT_GLOBAL the last stage hands element k of line l to
+// put(l, k, value) instead of writing buf.  Work items take the line index
+// fastest across threads, so when consecutive lines are consecutive in global
+// memory those accesses are coalesced.  buf is still the staging area between
+// the stages.
+template <bool INV, int N, int NLINES, int NT, int LS, int ES, bool IN_GLOBAL, bool OUT_GLOBAL, typename C,
+          typename Get, typename Put>
+__device__ __forceinline__ void smem_fft_io(C* buf, const C* tw, Get get, Put put) {
   using S = LineSplit<N>;
   constexpr int N1 = S::N1, N2 = S::N2;
   const int tid = threadIdx.x;
 
   if constexpr (N2 == 1) {
-    // single stage: a work item owns its whole line and writes it in place
+    // single stage: a work item owns its whole line
     constexpr int PA = (NLINES + NT - 1) / NT;
 #pragma unroll
     for (int s = 0; s < PA; ++s) {
@@ -50,11 +58,22 @@ __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
       if ((NLINES % NT) == 0 || it < NLINES) {
         C* base = buf + it * LS;
         C r[N1];
+        if constexpr (IN_GLOBAL) {
 #pragma unroll
-        for (int k = 0; k < N1; ++k) r[k] = base[k * ES];
+          for (int k = 0; k < N1; ++k) r[k] = get(it, k);
+        } else {
+#pragma unroll
+          for (int k = 0; k < N1; ++k) r[k] = base[k * ES];
+        }
         DFT<N1, INV>::run(r);
 #pragma unroll
-        for (int k = 0; k < N1; ++k) base[k * ES] = r[k];
+        for (int k = 0; k < N1; ++k) {
+          if constexpr (OUT_GLOBAL) {
+            put(it, k, r[k]);
+          } else {
+            base[k * ES] = r[k];
+          }
+        }
       }
     }
     __syncthreads();
@@ -72,8 +91,13 @@ __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
           const int l = it % NLINES, n2 = it / NLINES;
           C* base = buf + l * LS + n2 * ES;
           C ra[N1];
+          if constexpr (IN_GLOBAL) {
 #pragma unroll
-          for (int n1 = 0; n1 < N1; ++n1) ra[n1] = base[n1 * N2 * ES];
+            for (int n1 = 0; n1 < N1; ++n1) ra[n1] = get(l, n1 * N2 + n2);
+          } else {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) ra[n1] = base[n1 * N2 * ES];
+          }
           DFT<N1, INV>::run(ra);
 #pragma unroll
           for (int k1 = 1; k1 < N1; ++k1) {
@@ -88,7 +112,27 @@ __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
       __syncthreads();
     }
     // ---- stage B: items (line, k1) ----
-    {
+    if constexpr (OUT_GLOBAL) {
+      // results leave for global memory: no shared-memory hazards, so each
+      // thread runs its items one after another
+      constexpr int ITEMS = NLINES * N1;
+      constexpr int PB = (ITEMS + NT - 1) / NT;
+#pragma unroll 1
+      for (int s = 0; s < PB; ++s) {
+        const int it = tid + s * NT;
+        if ((ITEMS % NT) == 0 || it < ITEMS) {
+          const int l = it % NLINES, k1 = it / NLINES;
+          const C* base = buf + l * LS + k1 * N2 * ES;
+          C rb[N2];
+#pragma unroll
+          for (int n2 = 0; n2 < N2; ++n2) rb[n2] = base[n2 * ES];
+          DFT<N2, INV>::run(rb);
+#pragma unroll
+          for (int k2 = 0; k2 < N2; ++k2) put(l, k1 + N1 * k2, rb[k2]);
+        }
+      }
+      __syncthreads();
+    } else {
       using CK = Chunking<N1, NLINES, NT>;
       C rb[N2];
       int l = 0, k1 = 0;
@@ -115,6 +159,19 @@ __device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
       }
     }
   }
+}
+
+struct NoGet {
+  template <typename L, typename E> __device__ __forceinline__ int operator()(L, E) const { return 0; }
+};
+struct NoPut {
+  template <typename L, typename E, typename V> __device__ __forceinline__ void operator()(L, E, V) const {}
+};
+
+// The line DFTs entirely in shared memory (in place).
+template <bool INV, int N, int NLINES, int NT, int LS, int ES, typename C>
+__device__ __forceinline__ void smem_fft(C* buf, const C* tw) {
+  smem_fft_io<INV, N, NLINES, NT, LS, ES, false, false>(buf, tw, NoGet{}, NoPut{});
 }
 
 }  // namespace nfs

@@ -74,55 +74,6 @@ struct Lane {
   using V = typename std::conditional<EPV == 2, float4, C>::type;
 };
 
-// Bursts of global loads of Lane<C> vectors: thread t handles vectors t,
-// t + NT, ... (NV vectors in all), issued BATCH at a time before any is
-// consumed, so that every thread keeps BATCH requests in flight.
-// put(element_index, value) receives each complex element.
-template <int NV, int NT, int BATCH, typename C, typename Put>
-__device__ __forceinline__ void burst_load(const C* __restrict__ src, Put put) {
-  using V = typename Lane<C>::V;
-  constexpr int EPV = Lane<C>::EPV;
-  constexpr int PER = (NV + NT - 1) / NT;
-  const V* s = reinterpret_cast<const V*>(src);
-#pragma unroll
-  for (int b0 = 0; b0 < PER; b0 += BATCH) {
-    V r[BATCH];
-#pragma unroll
-    for (int b = 0; b < BATCH; ++b) {
-      const int v = (b0 + b) * NT + (int)threadIdx.x;
-      if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) r[b] = __ldg(s + v);
-    }
-#pragma unroll
-    for (int b = 0; b < BATCH; ++b) {
-      const int v = (b0 + b) * NT + (int)threadIdx.x;
-      if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) {
-        if constexpr (EPV == 2) {
-          put(2 * v, mk(r[b].x, r[b].y));
-          put(2 * v + 1, mk(r[b].z, r[b].w));
-        } else {
-          put(v, r[b]);
-        }
-      }
-    }
-  }
-}
-
-// Global stores of Lane<C> vectors taken from get(element_index).
-template <int NV, int NT, typename C, typename Get>
-__device__ __forceinline__ void burst_store(C* __restrict__ dst, Get get) {
-  using V = typename Lane<C>::V;
-  constexpr int EPV = Lane<C>::EPV;
-  V* d = reinterpret_cast<V*>(dst);
-  for (int v = (int)threadIdx.x; v < NV; v += NT) {
-    if constexpr (EPV == 2) {
-      const C a = get(2 * v), b = get(2 * v + 1);
-      d[v] = make_float4(a.x, a.y, b.x, b.y);
-    } else {
-      d[v] = get(v);
-    }
-  }
-}
-
 // Sum of one double per thread over the block (result valid in thread 0).
 template <int NT>
 __device__ __forceinline__ double block_sum_dbl(double v) {
@@ -366,9 +317,10 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
     __syncthreads();
   }
   smem_fft<true, NX, NY, NT, PITCH, 1>(plane, stx);  // along x (rows)
-  smem_fft<true, NY, NX, NT, 1, PITCH>(plane, sty);  // along y (columns)
+  // along y (columns), the results leaving for global memory from registers
   C* out = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
-  burst_store<NE / EPV, NT, C>(out, [&](int e) { return plane[(e / NX) * PITCH + (e % NX)]; });
+  smem_fft_io<true, NY, NX, NT, 1, PITCH, false, true>(plane, sty, NoGet{},
+                                                      [&](int i1, int i2, C v) { out[i2 * NX + i1] = v; });
 }
 
 // ---------------------------------------------------------------------------
@@ -432,12 +384,8 @@ __global__ void __launch_bounds__(NT, MINB)
 k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __restrict__ twz, int ncols,
                    R inv_n, const int* __restrict__ skip, BatchStrides bs) {
   using C = cplx<R>;
-  using V = typename Lane<C>::V;
-  constexpr int EPV = Lane<C>::EPV;
   constexpr int LINES = 6 * TX;
   constexpr int PITCH = LINES + 1;
-  constexpr int VPR = TX / EPV;             // 16-byte vectors per (field, z) run
-  constexpr int NV = 6 * N3 * VPR;          // vectors per CTA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* stw = buf + N3 * PITCH;
@@ -451,38 +399,14 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
   for (int i = threadIdx.x; i < N3; i += NT) stw[i] = twz[i];
   const int col0 = (blockIdx.x % tiles) * TX;
   const long long n = (long long)ncols * N3;
-  {
-    constexpr int PER = (NV + NT - 1) / NT;
-    constexpr int BATCH = PER < 8 ? PER : 8;
-#pragma unroll
-    for (int b0 = 0; b0 < PER; b0 += BATCH) {
-      V r[BATCH];
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b) {
-        const int v = (b0 + b) * NT + (int)threadIdx.x;
-        if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) {
-          const int cv = v % VPR, t = v / VPR, f = t % 6, z = t / 6;
-          r[b] = *(reinterpret_cast<const V*>(fld + f * n + (long long)z * ncols + col0) + cv);
-        }
-      }
-#pragma unroll
-      for (int b = 0; b < BATCH; ++b) {
-        const int v = (b0 + b) * NT + (int)threadIdx.x;
-        if (b0 + b < PER && ((NV % NT) == 0 || v < NV)) {
-          const int cv = v % VPR, t = v / VPR, f = t % 6, z = t / 6;
-          C* d = buf + z * PITCH + f * TX + cv * EPV;
-          if constexpr (EPV == 2) {
-            d[0] = mk(r[b].x, r[b].y);
-            d[1] = mk(r[b].z, r[b].w);
-          } else {
-            d[0] = r[b];
-          }
-        }
-      }
-    }
-  }
-  __syncthreads();
-  smem_fft<true, N3, LINES, NT, 1, PITCH>(buf, stw);
+  // line l = f * TX + c of the tile is field f, column col0 + c; its element
+  // z lives at fld[f n + z ncols + col0 + c] (consecutive lines, consecutive
+  // addresses within a field)
+  C* tile = fld + col0;
+  auto gaddr = [&](int l, int z) { return tile + (long long)(l / TX) * n + (long long)z * ncols + (l % TX); };
+  __syncthreads();  // twiddles
+  smem_fft_io<true, N3, LINES, NT, 1, PITCH, true, false>(buf, stw, [&](int l, int z) { return __ldg(gaddr(l, z)); },
+                                                         NoPut{});
   for (int idx = threadIdx.x; idx < N3 * TX; idx += NT) {
     const int c = idx % TX, z = idx / TX;
     C* row = buf + z * PITCH + c;
@@ -498,17 +422,8 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
     row[5 * TX] = wo[2];
   }
   __syncthreads();
-  smem_fft<false, N3, LINES, NT, 1, PITCH>(buf, stw);
-  for (int v = threadIdx.x; v < NV; v += NT) {
-    const int cv = v % VPR, t = v / VPR, f = t % 6, z = t / 6;
-    const C* s = buf + z * PITCH + f * TX + cv * EPV;
-    V* d = reinterpret_cast<V*>(fld + f * n + (long long)z * ncols + col0) + cv;
-    if constexpr (EPV == 2) {
-      *d = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
-    } else {
-      *d = s[0];
-    }
-  }
+  smem_fft_io<false, N3, LINES, NT, 1, PITCH, false, true>(buf, stw, NoGet{},
+                                                          [&](int l, int z, C v) { *gaddr(l, z) = v; });
 }
 
 // ---------------------------------------------------------------------------
@@ -545,12 +460,12 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
   const C* in = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
-  constexpr int PER = (NE / EPV + NT - 1) / NT;
-  burst_load<NE / EPV, NT, (PER < 12 ? PER : 12), C>(
-      in, [&](int e, C v) { plane[(e / NX) * PITCH + (e % NX)] = v; });
-  __syncthreads();
+  __syncthreads();  // twiddles
+  // the 2-D DFT along y first (columns, read from global memory straight into
+  // registers), then along x
+  smem_fft_io<false, NY, NX, NT, 1, PITCH, true, false>(plane, sty,
+                                                       [&](int i1, int i2) { return __ldg(in + i2 * NX + i1); }, NoPut{});
   smem_fft<false, NX, NY, NT, PITCH, 1>(plane, stx);
-  smem_fft<false, NY, NX, NT, 1, PITCH>(plane, sty);
   cl.sync();
   const C* src0 = cl.map_shared_rank(plane, 0);
   const C* src1 = cl.map_shared_rank(plane, 1);
