@@ -416,7 +416,10 @@ def run_ours(args):
                        "split_s": {"total": info.seconds_total, "cg": info.seconds_cg,
                                    "refine": info.seconds_refine, "ritz": info.seconds_ritz,
                                    "lanczos": info.seconds_total - info.seconds_cg - info.seconds_refine
-                                   - info.seconds_ritz}},
+                                   - info.seconds_ritz,
+                                   "lanczos_recurrence": info.seconds_recurrence,
+                                   "lanczos_orth": info.seconds_orth, "ritz_vectors": info.seconds_vectors},
+                       "reorthogonalisations": info.reorthogonalisations},
         "fp64": fp64,
         "roofline": roof,
         "cpu_baseline": cpu,

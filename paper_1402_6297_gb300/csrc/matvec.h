@@ -18,6 +18,7 @@ struct BatchStrides {
   long long sfld = 0;    // fld
   long long smat = 0;    // inv_phi, gam, inv_mu
   long long sstate = 0;  // cg_beta, dot_part
+  long long sbasis = 0;  // basis
   int slam = 0;          // lam
   int sskip = 0;         // skip
 };
@@ -38,6 +39,9 @@ struct MatvecArgs {
   int n1, n2, n3;
   R alpha, beta;
   const int* skip;        // device flag: when nonzero every pass returns at once
+  // optional table of the per-voxel basis, [c_x, c_y, c_z, x_x, x_y, x_z][n]
+  // (spectral order); nullptr: evaluated from the Lambda tables in the kernels
+  const cplx<R>* basis;
   cudaStream_t stream;
   // CG fusion (both optional, nullptr when unused):
   const cplx<R>* cg_r;    // pass 1 first forms u = cg_r + (*cg_beta) u in place
@@ -61,6 +65,11 @@ template <typename R> cudaError_t matvec_launch(const MatvecArgs<R>& a);
 template <typename R> cudaError_t matvec_launch_mask(const MatvecArgs<R>& a, int mask);
 // Split launches used by the eigenvector-gradient path: pass 1 only.
 template <typename R> cudaError_t pass1_launch(const MatvecArgs<R>& a);
+
+// The basis table for MatvecArgs<double>::basis: P problems (Lambda tables
+// at lam + p * slam, tables at basis + p * sbasis).
+cudaError_t basis_table_launch(const double2* lam, int n1, int n2, int n3, double alpha, double beta, double2* basis,
+                               int P, int slam, long long sbasis, cudaStream_t stream);
 
 // Gradient accumulation (complex128 only): inverse z-DFT of the six pass-1
 // fields and, per voxel, d_eps += scale * dA/deps, d_gamma += scale * dA/dgamma.

@@ -1,5 +1,6 @@
 // complex128 instantiation of the three-pass A_r product, and the eigenvalue
 // gradient pass that shares its pass-1 fields.
+#include <algorithm>
 #include "matvec_impl.cuh"
 
 namespace nfs {
@@ -111,6 +112,14 @@ cudaError_t grad_launch(const GradArgs& a) {
 #undef NFS_CASE
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t basis_table_launch(const double2* lam, int n1, int n2, int n3, double alpha, double beta, double2* basis,
+                               int P, int slam, long long sbasis, cudaStream_t stream) {
+  const long long total = (long long)n1 * n2 * n3 * P;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+  k_basis_table<double><<<blocks, 256, 0, stream>>>(lam, n1, n2, n3, alpha, beta, basis, P, slam, sbasis);
+  return cudaGetLastError();
 }
 
 }  // namespace nfs

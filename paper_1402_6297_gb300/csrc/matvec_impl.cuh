@@ -77,10 +77,10 @@ static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
     dim3 grid(3, 2, a.n3 * (a.P > 0 ? a.P : 1));
     if (which == 1) {
       k_pass1_assemble_ifft_xy<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
-          a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.bs);
+          a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.basis, a.bs);
     } else {
       k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
-          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.u, a.dot_part, a.bs);
+          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.u, a.dot_part, a.basis, a.bs);
     }
     return cudaGetLastError();
   } else {

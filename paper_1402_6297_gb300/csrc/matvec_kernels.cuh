@@ -119,6 +119,43 @@ __device__ __forceinline__ void make_basis(cplx<R> a1, cplx<R> a2, cplx<R> a3, R
   B.x[2] = cscale(csub(cmulc(B.c[1], a1), cmulc(B.c[0], a2)), rq);
 }
 
+// The basis of spectral voxel v: from the table when there is one, else from
+// the Lambda tables.
+template <typename R>
+__device__ __forceinline__ void voxel_basis(const cplx<R>* __restrict__ table, long long n, long long v, cplx<R> a1,
+                                            cplx<R> a2, cplx<R> a3, R al, R be, Basis<R>& B) {
+  if (table != nullptr) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      B.c[k] = table[k * n + v];
+      B.x[k] = table[(3 + k) * n + v];
+    }
+  } else {
+    make_basis<R>(a1, a2, a3, al, be, B);
+  }
+}
+
+// Table of the basis (complex128 products use it: double-precision square
+// roots are scarce on this GPU).  Grid-stride over P x n voxels.
+template <typename R>
+__global__ void k_basis_table(const cplx<R>* __restrict__ lam, int n1, int n2, int n3, R al, R be,
+                              cplx<R>* __restrict__ table, int P, int slam, long long sbasis) {
+  const long long n = (long long)n1 * n2 * n3;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n * P; g += (long long)gridDim.x * blockDim.x) {
+    const long long p = g / n, v = g % n;
+    const int i1 = (int)(v % n1), i2 = (int)((v / n1) % n2), i3 = (int)(v / ((long long)n1 * n2));
+    const cplx<R>* L = lam + p * slam;
+    Basis<R> B;
+    make_basis<R>(L[i1], L[n1 + i2], L[n1 + n2 + i3], al, be, B);
+    cplx<R>* t = table + p * sbasis;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      t[k * n + v] = B.c[k];
+      t[(3 + k) * n + v] = B.x[k];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pass 1
 // ---------------------------------------------------------------------------
@@ -160,7 +197,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
                          const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                          const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
                          const int* __restrict__ skip, const cplx<R>* __restrict__ cg_r,
-                         const double* __restrict__ cg_beta, BatchStrides bs) {
+                         const double* __restrict__ cg_beta, const cplx<R>* __restrict__ basis, BatchStrides bs) {
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
@@ -178,6 +215,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
   u += prob * bs.su;
   fld += prob * bs.sfld;
   lam += (long long)prob * bs.slam;
+  if (basis != nullptr) basis += prob * bs.sbasis;
   if (cg_r != nullptr) {
     cg_r += prob * bs.su;
     cg_beta += prob * bs.sstate;
@@ -252,7 +290,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
         }
         const int i1 = e % NX, i2 = e / NX;
         Basis<R> B;
-        make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
+        voxel_basis<R>(basis, n, (long long)i3 * NE + e, lam[i1], lam[NX + i2], a3, alpha, beta, B);
         C o[3];
         if (grp == 0) {
           // p^ = -c u1a + x u1b
@@ -435,7 +473,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
                        const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                        const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
                        const int* __restrict__ skip, const cplx<R>* __restrict__ u, double* __restrict__ dot_part,
-                       BatchStrides bs) {
+                       const cplx<R>* __restrict__ basis, BatchStrides bs) {
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
@@ -453,6 +491,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   fld += prob * bs.sfld;
   Au += prob * bs.su;
   lam += (long long)prob * bs.slam;
+  if (basis != nullptr) basis += prob * bs.sbasis;
   if (dot_part != nullptr) {
     u += prob * bs.su;
     dot_part += prob * bs.sstate;
@@ -491,7 +530,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
       const int s = i2 * PITCH + i1;
       const C f[3] = {src0[s], src1[s], src2[s]};
       Basis<R> B;
-      make_basis<R>(lam[i1], lam[NX + i2], a3, alpha, beta, B);
+      voxel_basis<R>(basis, n, (long long)i3 * NE + e, lam[i1], lam[NX + i2], a3, alpha, beta, B);
       if (grp == 0) {
         // P_r^* f = [-sum conj(c) f ; sum conj(x) f]
         r0[h] = cneg(cadd(cadd(cmulc(B.c[0], f[0]), cmulc(B.c[1], f[1])), cmulc(B.c[2], f[2])));

@@ -61,6 +61,7 @@ struct nfs_ctx {
   // material, per problem (stride mat_len): inv_phi [3n] | gam [3n or n] | inv_mu [3n]
   double* mat64 = nullptr;
   float* mat32 = nullptr;
+  double2* basis64 = nullptr;  // per problem [6][n]: c and x of every voxel (complex128 products)
   // workspaces, per problem
   void* fld = nullptr;  // 6n complex128 each (complex64 uses 12n entries of it)
   double2 *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *Ap64 = nullptr, *t64 = nullptr, *t64b = nullptr;
@@ -176,8 +177,10 @@ nfs::MatvecArgs<double> margs<double>(nfs_ctx* c, const double2* u, double2* Au,
   a.kind = c->kind; a.ax_a = c->ax_a; a.ax_b = c->ax_b;
   a.n1 = c->n1; a.n2 = c->n2; a.n3 = c->n3; a.alpha = c->opt.alpha; a.beta = c->opt.beta;
   a.skip = skip; a.stream = c->stream;
+  a.basis = c->basis64;
   a.P = c->P;
   a.bs = strides(c, 6 * c->n);
+  a.bs.sbasis = 6 * c->n;
   return a;
 }
 
@@ -903,7 +906,7 @@ void free_ctx(nfs_ctx* c) {
   if (!c) return;
   for (GraphEntry& g : c->graphs) cudaGraphExecDestroy(g.exec);
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
-                  c->mat64, c->mat32, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
+                  c->mat64, c->mat32, c->basis64, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
                   c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
                   c->MV32lo, c->dY};
   for (void* p : ptrs)
@@ -1136,6 +1139,8 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
       CKC(cudaMemcpy(c->mat32 + (size_t)p * ml, m32.data(), ml * sizeof(float), cudaMemcpyHostToDevice));
     }
   }
+  TRYC(dalloc(c, &c->basis64, (size_t)P * 6 * c->n));
+  CKC(nfs::basis_table_launch(c->lam64, n1, n2, n3, o.alpha, o.beta, c->basis64, P, nl, 6 * c->n, 0));
   const size_t PN = (size_t)P * c->N;
   TRYC(dalloc(c, (double2**)&c->fld, (size_t)P * 6 * c->n));
   TRYC(dalloc(c, &c->x64, PN));
