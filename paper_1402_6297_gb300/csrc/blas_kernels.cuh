@@ -503,27 +503,25 @@ __global__ void k_shadow_axpy(double2* __restrict__ w, double2* __restrict__ Mw,
 // arithmetic, scarce on this GPU, is used only for the per-block totals.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = __fmul_rn(a, b);
-  e = __fmaf_rn(a, b, -p);
+// Error-free transformations (TwoProduct by FMA; TwoSum, Knuth) on (real,
+// imaginary) pairs, both halves in one packed f32x2 instruction:
+// p + e = a * b and s + e = a + b exactly, per half.
+__device__ __forceinline__ void two_prod_x2(float2 a, float2 b, float2& p, float2& e) {
+  p = mul_x2(a, b);
+  e = fma_x2(a, b, make_float2(-p.x, -p.y));
 }
-
-// s + e = a + b exactly
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+__device__ __forceinline__ void two_sum_x2(float2 a, float2 b, float2& s, float2& e) {
+  s = add_x2(a, b);
+  const float2 bb = sub_x2(s, a);
+  e = add_x2(sub_x2(a, sub_x2(s, bb)), sub_x2(b, bb));
 }
-
-// running sum hi + lo (exact additions into hi, errors into lo)
-struct DSAcc {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    float e;
-    two_sum(hi, x, hi, e);
-    lo = __fadd_rn(lo, e);
+struct DSAccX2 {
+  float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 x) {
+    float2 e;
+    two_sum_x2(hi, x, hi, e);
+    lo = add_x2(lo, e);
   }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 __device__ __forceinline__ float2 split_lo(double2 v, float2 hi) {
@@ -563,45 +561,39 @@ k_exact_dots(const float2* __restrict__ Shi, const float2* __restrict__ Slo, lon
   whi += (long long)p * N;
   wlo += (long long)p * N;
   const int j0 = blockIdx.y * G;
-  DSAcc re[G], im[G];
-  float sre[G], sim[G];
+  // per vector: the exact sum of the hi x hi products (real, imaginary) and
+  // an ordinary sum of their rounding errors and the hi x lo, lo x hi terms
+  DSAccX2 acc[G];
+  float2 small[G];
 #pragma unroll
-  for (int g = 0; g < G; ++g) sre[g] = sim[g] = 0.f;
+  for (int g = 0; g < G; ++g) small[g] = make_float2(0.f, 0.f);
   for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
     const float2 bh = whi[i], bl = wlo[i];
+    // conj(a) b = (ar br + ai bi, ar bi - ai br) = ar (br, bi) + ai (bi, -br)
+    const float2 bh2 = make_float2(bh.y, -bh.x), bl2 = make_float2(bl.y, -bl.x);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       if (j0 + g < m) {
         const float2 ah = Shi[(long long)(j0 + g) * N + i], al = Slo[(long long)(j0 + g) * N + i];
-        // conj(a) b: re = ar br + ai bi, im = ar bi - ai br
-        float p1, e1, p2, e2, p3, e3, p4, e4;
-        two_prod(ah.x, bh.x, p1, e1);
-        two_prod(ah.y, bh.y, p2, e2);
-        two_prod(ah.x, bh.y, p3, e3);
-        two_prod(ah.y, bh.x, p4, e4);
-        re[g].add(p1);
-        re[g].add(p2);
-        im[g].add(p3);
-        im[g].add(-p4);
-        float t = e1 + e2;
-        t = __fmaf_rn(ah.x, bl.x, t);
-        t = __fmaf_rn(al.x, bh.x, t);
-        t = __fmaf_rn(ah.y, bl.y, t);
-        t = __fmaf_rn(al.y, bh.y, t);
-        sre[g] += t;
-        float u = e3 - e4;
-        u = __fmaf_rn(ah.x, bl.y, u);
-        u = __fmaf_rn(al.x, bh.y, u);
-        u = __fmaf_rn(-ah.y, bl.x, u);
-        u = __fmaf_rn(-al.y, bh.x, u);
-        sim[g] += u;
+        const float2 ax = make_float2(ah.x, ah.x), ay = make_float2(ah.y, ah.y);
+        float2 p1, e1, p2, e2;
+        two_prod_x2(ax, bh, p1, e1);
+        two_prod_x2(ay, bh2, p2, e2);
+        acc[g].add(p1);
+        acc[g].add(p2);
+        float2 t = add_x2(e1, e2);
+        t = fma_x2(ax, bl, t);
+        t = fma_x2(make_float2(al.x, al.x), bh, t);
+        t = fma_x2(ay, bl2, t);
+        t = fma_x2(make_float2(al.y, al.y), bh2, t);
+        small[g] = add_x2(small[g], t);
       }
     }
   }
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    const double sr = block_sum<kRedThreads>(re[g].value() + (double)sre[g]);
-    const double si = block_sum<kRedThreads>(im[g].value() + (double)sim[g]);
+    const double sr = block_sum<kRedThreads>((double)acc[g].hi.x + (double)acc[g].lo.x + (double)small[g].x);
+    const double si = block_sum<kRedThreads>((double)acc[g].hi.y + (double)acc[g].lo.y + (double)small[g].y);
     if (threadIdx.x == 0 && j0 + g < m) {
       const long long o = (((long long)p * m + j0 + g) * gridDim.x + blockIdx.x) * 2;
       part[o] = sr;
