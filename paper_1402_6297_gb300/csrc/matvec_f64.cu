@@ -80,7 +80,7 @@ k_grad_z(const double2* __restrict__ fld, const double2* __restrict__ twz, int n
 template <int N3>
 static cudaError_t grad_prep_n3() {
   constexpr int TX = z_tile(N3, 16);
-  constexpr int NT = z_threads(N3);
+  constexpr int NT = z_threads(N3, 16);
   return cudaFuncSetAttribute(k_grad_z<N3, TX, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)z_smem<double, N3>());
 }
@@ -88,7 +88,7 @@ static cudaError_t grad_prep_n3() {
 template <int N3>
 static cudaError_t grad_launch_n3(const GradArgs& a) {
   constexpr int TX = z_tile(N3, 16);
-  constexpr int NT = z_threads(N3);
+  constexpr int NT = z_threads(N3, 16);
   const int ncols = a.n1 * a.n2;
   k_grad_z<N3, TX, NT><<<ncols / TX, NT, z_smem<double, N3>(), a.stream>>>(
       a.fld, a.tw3, ncols, a.inv_phi, a.gam, a.kind, a.ax_a, a.ax_b, a.scale, a.d_eps, a.d_gamma);

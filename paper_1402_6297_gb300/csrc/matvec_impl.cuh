@@ -12,10 +12,18 @@ __host__ __device__ constexpr int plane_threads(int N) {
        : N == 48 ? 384 : N == 64 ? 256 : N == 96 ? 384 : 512;
 }
 // xy columns per CTA of the z pass, per z length and element size.
+#ifndef NFS_ZTILE_C64
+#define NFS_ZTILE_C64 16
+#endif
+#ifndef NFS_ZTHREADS_C64
+#define NFS_ZTHREADS_C64 384
+#endif
 __host__ __device__ constexpr int z_tile(int N3, int csize) {
-  return (csize == 16 && N3 >= 96) ? 8 : 16;
+  return (csize == 16 && N3 >= 96) ? 8 : ((csize == 8 && N3 >= 48 && N3 <= 96) ? NFS_ZTILE_C64 : 16);
 }
-__host__ __device__ constexpr int z_threads(int N3) { return N3 == 128 ? 512 : 384; }
+__host__ __device__ constexpr int z_threads(int N3, int csize) {
+  return N3 == 128 ? 512 : ((csize == 8 && N3 >= 48 && N3 <= 96) ? NFS_ZTHREADS_C64 : 384);
+}
 // Minimum resident CTAs per SM requested from the compiler (caps registers so
 // that three CTAs share an SM and overlap one's memory phase with the others'
 // shared-memory FFTs; 96^3 complex64 planes are 75 KB, three fit in 228 KB).
@@ -65,7 +73,7 @@ static cudaError_t plane_prepare() {
 template <typename R, int N3>
 static cudaError_t z_prepare() {
   constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
-  constexpr int NT = z_threads(N3);
+  constexpr int NT = z_threads(N3, (int)sizeof(cplx<R>));
   return cudaFuncSetAttribute(k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)z_smem<R, N3>());
 }
@@ -91,7 +99,7 @@ static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
 template <typename R, int N3>
 static cudaError_t z_launch(const MatvecArgs<R>& a) {
   constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
-  constexpr int NT = z_threads(N3);
+  constexpr int NT = z_threads(N3, (int)sizeof(cplx<R>));
   const int ncols = a.n1 * a.n2;
   MatView<R> mv{a.inv_phi, a.gam, a.inv_mu, a.kind, a.ax_a, a.ax_b, (long long)ncols * a.n3};
   const R inv_n = (R)(1.0 / ((double)ncols * (double)a.n3));

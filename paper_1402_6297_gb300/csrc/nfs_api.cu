@@ -85,6 +85,7 @@ struct nfs_ctx {
   float2* MV32lo = nullptr;  // FP64 remainder of the MV32 shadow
   int vcap = 0;
   double* dY = nullptr;  // rotation coefficients
+  int ncv_set = 0;       // basis size chosen by a batch for this context (0: own default)
   size_t dY_len = 0;
   std::vector<GraphEntry> graphs;
   long long bytes = 0;
@@ -625,14 +626,20 @@ int apply_Br_basis(nfs_ctx* c, int j, double2* out) {
   return NFS_OK;
 }
 
+// Device bytes per basis vector of a context: V, A_rV (complex128), their
+// complex64 shadows and the remainder of the A_rV shadow.
+double basis_bytes_per_vector(const nfs_ctx* c) { return (double)c->P * c->N * (16 + 16 + 8 + 8 + 8); }
+
+int wanted_ncv(int nev) { return std::max(std::max(3 * nev, 2 * nev + 2), std::min(12 * nev, 320)); }
+
 // Default basis size: generous (device memory is plentiful and restarts cost
 // FP64 basis rotations), capped by half of the free device memory.
 int default_ncv(nfs_ctx* c, int nev) {
-  int m = std::max(std::max(3 * nev, 2 * nev + 2), std::min(12 * nev, 320));
+  if (c->ncv_set > 0) return c->ncv_set;
+  int m = wanted_ncv(nev);
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-    const double per = (double)c->P * c->N * (16 + 16 + 8 + 8 + 8);
-    const int cap = (int)std::max(0.0, 0.5 * (double)fr / per) - 1;
+    const int cap = (int)std::max(0.0, 0.5 * (double)fr / basis_bytes_per_vector(c)) - 1;
     if (cap < m) m = std::max(cap, 2 * nev + 2);
   }
   return m;
@@ -1422,6 +1429,22 @@ extern "C" int nfs_eigs_batch(nfs_batch* b, int nev, double* omega, nfs_eigs_inf
     om[i].assign((size_t)c->P * nev, 0.0);
     inf[i].assign(c->P, nfs_eigs_info{});
     TRY(join_caller(c));
+  }
+  // the classes run concurrently: one basis size for all, within 80% of the
+  // free device memory together, and the bases allocated here, in turn
+  // (restarts cost accuracy as well as time: each assumes the Lanczos relation
+  // of the inexact solves to hold exactly)
+  if (b->classes[0]->opt.ncv <= 0) {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    double per = 0.0;
+    for (nfs_ctx* c : b->classes) per += basis_bytes_per_vector(c);
+    int m = std::min(wanted_ncv(nev), (int)std::max(0.0, 0.8 * (double)fr / per) - 1);
+    m = std::max(m, 2 * nev + 2);
+    for (nfs_ctx* c : b->classes) {
+      c->ncv_set = (int)std::min<long long>(m, c->N - 1);
+      TRY(ensure_basis(c, c->ncv_set));
+    }
   }
   // one host thread per grid class; each drives its own stream
   std::vector<std::thread> th;
