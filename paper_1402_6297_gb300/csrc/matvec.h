@@ -65,6 +65,8 @@ template <typename R> cudaError_t matvec_launch(const MatvecArgs<R>& a);
 template <typename R> cudaError_t matvec_launch_mask(const MatvecArgs<R>& a, int mask);
 // Split launches used by the eigenvector-gradient path: pass 1 only.
 template <typename R> cudaError_t pass1_launch(const MatvecArgs<R>& a);
+// Number of p^* A p partials a CG product emits per problem (dot_part entries).
+template <typename R> int matvec_dot_partials(int n1, int n2, int n3);
 
 // The basis table for MatvecArgs<double>::basis: P problems (Lambda tables
 // at lam + p * slam, tables at basis + p * sbasis).

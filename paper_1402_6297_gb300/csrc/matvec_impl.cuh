@@ -3,6 +3,7 @@
 #pragma once
 #include "matvec.h"
 #include "matvec_kernels.cuh"
+#include "matvec_split.cuh"
 
 namespace nfs {
 
@@ -53,11 +54,43 @@ constexpr bool plane_fits() {
   return plane_smem<R, NX>() <= kMaxDynSmem;
 }
 
+// Planes that do not fit run the five-pass product (matvec_split.cuh):
+// tiles of kSplitRows rows (all three components) and kSplitCols columns.
+constexpr int kSplitRows = 32;
+constexpr int kSplitCols = 16;
+constexpr int kSplitRowThreads = 512;
+constexpr int kSplitColThreads = 128;
+template <typename R, int NX>
+constexpr size_t split_row_smem() {
+  return (size_t)(3 * kSplitRows * (NX + 1) + NX) * sizeof(cplx<R>);
+}
+template <typename R, int NY>
+constexpr size_t split_col_smem() {
+  return (size_t)(NY * (kSplitCols + 1) + NY) * sizeof(cplx<R>);
+}
+template <typename R, int NX>
+constexpr bool split_fits() {
+  return !plane_fits<R, NX>() && NX % kSplitRows == 0 && NX % kSplitCols == 0 &&
+         split_row_smem<R, NX>() <= kMaxDynSmem;
+}
+
 #define NFS_FOR_EACH_SIZE(M) M(8) M(12) M(16) M(24) M(32) M(48) M(64) M(96) M(128)
 
 template <typename R, int NX>
 static cudaError_t plane_prepare() {
-  if constexpr (plane_fits<R, NX>()) {
+  if constexpr (split_fits<R, NX>()) {
+    cudaError_t e = cudaFuncSetAttribute(k_pass1a_assemble_fft_x<R, NX, kSplitRows, kSplitRowThreads>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_row_smem<R, NX>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pass3b_fft_x_project<R, NX, kSplitRows, kSplitRowThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_row_smem<R, NX>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_fft_y_columns<true, R, NX, kSplitCols, kSplitColThreads>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_col_smem<R, NX>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fft_y_columns<false, R, NX, kSplitCols, kSplitColThreads>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_col_smem<R, NX>());
+  } else if constexpr (plane_fits<R, NX>()) {
     constexpr int NT = plane_threads(NX);
     cudaError_t e = cudaFuncSetAttribute(k_pass1_assemble_ifft_xy<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<R, NX>());
@@ -80,7 +113,24 @@ static cudaError_t z_prepare() {
 
 template <typename R, int NX>
 static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
-  if constexpr (plane_fits<R, NX>()) {
+  if constexpr (split_fits<R, NX>()) {
+    const int P = a.P > 0 ? a.P : 1;
+    const dim3 rows(a.n2 / kSplitRows, 2, a.n3 * P), cols(a.n1 / kSplitCols, 6, a.n3 * P);
+    if (which == 1) {
+      k_pass1a_assemble_fft_x<R, NX, kSplitRows, kSplitRowThreads>
+          <<<rows, kSplitRowThreads, split_row_smem<R, NX>(), a.stream>>>(
+              a.u, a.fld, a.lam, a.tw1, a.n2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.basis, a.bs);
+      k_fft_y_columns<true, R, NX, kSplitCols, kSplitColThreads>
+          <<<cols, kSplitColThreads, split_col_smem<R, NX>(), a.stream>>>(a.fld, a.tw2, a.n1, a.n3, a.skip, a.bs);
+    } else {
+      k_fft_y_columns<false, R, NX, kSplitCols, kSplitColThreads>
+          <<<cols, kSplitColThreads, split_col_smem<R, NX>(), a.stream>>>(a.fld, a.tw2, a.n1, a.n3, a.skip, a.bs);
+      k_pass3b_fft_x_project<R, NX, kSplitRows, kSplitRowThreads>
+          <<<rows, kSplitRowThreads, split_row_smem<R, NX>(), a.stream>>>(
+              a.fld, a.Au, a.lam, a.tw1, a.n2, a.n3, a.alpha, a.beta, a.skip, a.u, a.dot_part, a.basis, a.bs);
+    }
+    return cudaGetLastError();
+  } else if constexpr (plane_fits<R, NX>()) {
     constexpr int NT = plane_threads(NX);
     dim3 grid(3, 2, a.n3 * (a.P > 0 ? a.P : 1));
     if (which == 1) {
@@ -119,7 +169,7 @@ static inline bool size_ok(int n) {
 template <typename R>
 static bool plane_fits_rt(int n) {
   switch (n) {
-#define NFS_CASE(N) case N: return plane_fits<R, N>();
+#define NFS_CASE(N) case N: return plane_fits<R, N>() || split_fits<R, N>();
     NFS_FOR_EACH_SIZE(NFS_CASE)
 #undef NFS_CASE
     default: return false;
@@ -198,11 +248,27 @@ cudaError_t pass1_launch(const MatvecArgs<R>& a) {
   return plane_dispatch<R>(a, 1);
 }
 
+template <typename R>
+static bool split_rt(int n) {
+  switch (n) {
+#define NFS_CASE(N) case N: return split_fits<R, N>();
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return false;
+}
+
+template <typename R>
+int matvec_dot_partials(int n1, int n2, int n3) {
+  return split_rt<R>(n1) ? (n2 / kSplitRows) * 2 * n3 : 6 * n3;
+}
+
 #define NFS_INSTANTIATE_MATVEC(R)                                            \
   template bool matvec_supported<R>(int, int, int);                        \
   template cudaError_t matvec_prepare<R>(int, int, int);                   \
   template cudaError_t matvec_launch<R>(const MatvecArgs<R>&);             \
   template cudaError_t matvec_launch_mask<R>(const MatvecArgs<R>&, int);   \
-  template cudaError_t pass1_launch<R>(const MatvecArgs<R>&);
+  template cudaError_t pass1_launch<R>(const MatvecArgs<R>&);               \
+  template int matvec_dot_partials<R>(int, int, int);
 
 }  // namespace nfs

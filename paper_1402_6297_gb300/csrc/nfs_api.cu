@@ -343,7 +343,8 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
   nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(r, r, c->N, c->st->part_a, nfs::kStateDoubles,
                                                                    nullptr, 0);
   TRY(put_small(c, s, 0, tol2));
-  nfs::k_cg_init<<<c->P, kRedThreads, 0, s>>>(c->st, c->d_small, maxit, 6 * c->n3);
+  nfs::k_cg_init<<<c->P, kRedThreads, 0, s>>>(c->st, c->d_small, maxit,
+                                               nfs::matvec_dot_partials<R>(c->n1, c->n2, c->n3));
   CK(cudaGetLastError());
   c->launches += 2;
   cudaGraphExec_t exec = nullptr;

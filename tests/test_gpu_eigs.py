@@ -82,6 +82,23 @@ def test_homogeneous_closed_form(nfs):
     ctx.close()
 
 
+def test_homogeneous_closed_form_128_mixed(nfs):
+    """Section 5.1 closed form at 128^3 on the mixed path (its refinement
+    products run the five-pass complex128 product of planes that do not fit
+    in shared memory)."""
+    g = (128, 128, 128)
+    k = (0.25, 0.1, 0.4)
+    ctx = nfs.Context(g, k, wl.homogeneous(g), precision="mixed")
+    omega, _, _ = ctx.eigs(6, vectors=False)
+    n1 = 128
+    i = np.arange(n1)
+    s = [4 * np.sin(np.pi * (i + kk) / n1) ** 2 * n1 ** 2 for kk in k]
+    disp = np.sqrt(s[2][:, None, None] + s[1][None, :, None] + s[0][None, None, :]).ravel()
+    ref = np.sort(np.concatenate([disp, disp]))[:6]
+    assert np.abs((omega - ref) / ref).max() < 1e-8
+    ctx.close()
+
+
 def test_eig_gradient_vs_oracle(nfs):
     """Adjoint gradient of omega_1 + 2 omega_2 w.r.t. per-component eps and
     gamma against the oracle's pencil perturbation formula (8^3, random

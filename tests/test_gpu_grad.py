@@ -82,3 +82,31 @@ def test_per_voxel_gradient_large_step(ag):
         fd = (fp - fm) / (2 * h)
         an = float(eps.grad[v])
         assert abs(fd - an) <= 1e-4 * abs(an) + 1e-10, (v, fd, an)
+
+
+def test_uniform_direction_derivative_128(lib):
+    """At 128^3 (five-pass complex128 pass 1 inside the gradient): the sum of
+    d(omega_1 + ... + omega_5)/d eps over every voxel and component against a
+    central difference of eigensolves with all of eps shifted by +-h.  A
+    per-voxel step would move omega by less than the solver's accuracy; the
+    uniform direction moves the sum by ~1e-4 at h = 1e-4."""
+    nfs = lib
+    w = wl.workload("field128")
+    g, k, med = w["grid"], w["kdota"], w["medium"]
+    opts = dict(precision="mixed", cg_tol=1e-11, eig_tol=1e-11)
+    ctx = nfs.Context(g, k, med, **opts)
+    omega, Y, _ = ctx.eigs(6)
+    assert omega[4] < omega[5] * (1 - 1e-6)
+    d_eps, _ = ctx.eig_grad(Y[:5].contiguous(), np.ones(5))
+    an = float(d_eps.sum())
+    ctx.close()
+    h = 1e-4
+    f = []
+    for sgn in (1, -1):
+        m2 = wl.Medium(med.grid, med.kind, med.eps + sgn * h, med.gamma, med.mu, med.axes)
+        c2 = nfs.Context(g, k, m2, **opts)
+        om2, _, _ = c2.eigs(6, vectors=False)
+        f.append(float(om2[:5].sum()))
+        c2.close()
+    fd = (f[0] - f[1]) / (2 * h)
+    assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)

@@ -158,3 +158,20 @@ def test_matvec_full_size_96(nfs):
     got32 = ctx.matvec(torch.from_numpy(u.astype(np.complex64)).cuda()).cpu().numpy()
     assert rel_err(got32, ref) < 2e-5
     ctx.close()
+
+
+def test_matvec_full_size_128(nfs):
+    """Full-size parity at 128^3 (smoothed chiral field): the complex128
+    product runs the five-pass form (a 128 x 128 complex128 plane does not fit
+    in shared memory), the complex64 one the three-pass form."""
+    w = wl.workload("field128")
+    grid, med = w["grid"], w["medium"]
+    ctx = nfs.Context(grid, w["kdota"], med, precision="mixed")
+    orc = nfgep.NFGEP(grid, w["kdota"], med)
+    u = wl.random_complex(4 * ctx.n, 33)
+    ref = orc.Ar(u)
+    got64 = ctx.matvec(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel_err(got64, ref) < 1e-12
+    got32 = ctx.matvec(torch.from_numpy(u.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel_err(got32, ref) < 2e-5
+    ctx.close()
