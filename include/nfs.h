@@ -64,6 +64,8 @@ extern "C" {
 
 #define NFS_C128 0        /* vector element type: double2                         */
 #define NFS_C64  1        /* vector element type: float2                          */
+#define NFS_C128_DS 2     /* double2 vectors, product in double-single arithmetic
+                           * (float pairs, ~1e-14; mixed contexts, nfs_matvec only) */
 
 typedef struct nfs_ctx nfs_ctx;
 

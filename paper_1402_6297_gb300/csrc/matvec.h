@@ -73,6 +73,12 @@ template <typename R> int matvec_dot_partials(int n1, int n2, int n3);
 cudaError_t basis_table_launch(const double2* lam, int n1, int n2, int n3, double alpha, double beta, double2* basis,
                                int P, int slam, long long sbasis, cudaStream_t stream);
 
+// Double-single element conversions (matvec_df.cu); `count` reals, in and out
+// may alias for df_to_double.
+struct df;
+cudaError_t double_to_df(const double* in, df* out, long long count, cudaStream_t s);
+cudaError_t df_to_double(const df* in, double* out, long long count, cudaStream_t s);
+
 // Gradient accumulation (complex128 only): inverse z-DFT of the six pass-1
 // fields and, per voxel, d_eps += scale * dA/deps, d_gamma += scale * dA/dgamma.
 struct GradArgs {

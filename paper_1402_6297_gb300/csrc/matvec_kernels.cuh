@@ -253,7 +253,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
     for (int b = 0; b < PER; ++b) {
       const int v = b * NT + (int)threadIdx.x;
       if (v < nv) {
-        const V qa = __ldg(rva + v), qb = __ldg(rvb + v);
+        const V qa = ldg_c(rva + v), qb = ldg_c(rvb + v);
         if constexpr (EPV == 2) {
           ra[b] = make_float4(qa.x + bt * ra[b].x, qa.y + bt * ra[b].y, qa.z + bt * ra[b].z, qa.w + bt * ra[b].w);
           rb[b] = make_float4(qb.x + bt * rb[b].x, qb.y + bt * rb[b].y, qb.z + bt * rb[b].z, qb.w + bt * rb[b].w);
@@ -443,7 +443,7 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
   C* tile = fld + col0;
   auto gaddr = [&](int l, int z) { return tile + (long long)(l / TX) * n + (long long)z * ncols + (l % TX); };
   __syncthreads();  // twiddles
-  smem_fft_io<true, N3, LINES, NT, 1, PITCH, true, false>(buf, stw, [&](int l, int z) { return __ldg(gaddr(l, z)); },
+  smem_fft_io<true, N3, LINES, NT, 1, PITCH, true, false>(buf, stw, [&](int l, int z) { return ldg_c(gaddr(l, z)); },
                                                          NoPut{});
   for (int idx = threadIdx.x; idx < N3 * TX; idx += NT) {
     const int c = idx % TX, z = idx / TX;
@@ -503,7 +503,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   // the 2-D DFT along y first (columns, read from global memory straight into
   // registers), then along x
   smem_fft_io<false, NY, NX, NT, 1, PITCH, true, false>(plane, sty,
-                                                       [&](int i1, int i2) { return __ldg(in + i2 * NX + i1); }, NoPut{});
+                                                       [&](int i1, int i2) { return ldg_c(in + i2 * NX + i1); }, NoPut{});
   smem_fft<false, NX, NY, NT, PITCH, 1>(plane, stx);
   cl.sync();
   const C* src0 = cl.map_shared_rank(plane, 0);

@@ -141,7 +141,7 @@ k_pass3b_fft_x_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   for (int idx = threadIdx.x; idx < LINES * NX; idx += NT) {
     const int l = idx / NX, i1 = idx % NX;
     const int k = l / RT, r = l % RT;
-    tile[l * PITCH + i1] = __ldg(fld + ((long long)(grp * 3 + k) * n3 + i3) * NE + (long long)(row0 + r) * NX + i1);
+    tile[l * PITCH + i1] = ldg_c(fld + ((long long)(grp * 3 + k) * n3 + i3) * NE + (long long)(row0 + r) * NX + i1);
   }
   __syncthreads();
   smem_fft<false, NX, LINES, NT, PITCH, 1>(tile, stx);  // along x

@@ -27,6 +27,7 @@
 
 #include "../../include/nfs.h"
 #include "blas_kernels.cuh"
+#include "dfloat.cuh"
 #include "host_eig.h"
 #include "matvec.h"
 
@@ -62,6 +63,12 @@ struct nfs_ctx {
   double* mat64 = nullptr;
   float* mat32 = nullptr;
   double2* basis64 = nullptr;  // per problem [6][n]: c and x of every voxel (complex128 products)
+  // double-single copies of the tables, material and basis (mixed contexts:
+  // the refinement residual products)
+  nfs::dfc* lamdf = nullptr;
+  nfs::dfc* twdf[3] = {nullptr, nullptr, nullptr};
+  nfs::df* matdf = nullptr;
+  nfs::dfc* basisdf = nullptr;
   // workspaces, per problem
   void* fld = nullptr;  // 6n complex128 each (complex64 uses 12n entries of it)
   double2 *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *Ap64 = nullptr, *t64 = nullptr, *t64b = nullptr;
@@ -199,6 +206,22 @@ nfs::MatvecArgs<float> margs<float>(nfs_ctx* c, const float2* u, float2* Au, con
   return a;
 }
 
+template <>
+nfs::MatvecArgs<nfs::df> margs<nfs::df>(nfs_ctx* c, const nfs::dfc* u, nfs::dfc* Au, const int* skip) {
+  nfs::MatvecArgs<nfs::df> a{};
+  a.u = u; a.Au = Au; a.fld = (nfs::dfc*)c->fld; a.lam = c->lamdf;
+  a.tw1 = c->twdf[0]; a.tw2 = c->twdf[1]; a.tw3 = c->twdf[2];
+  a.inv_phi = c->matdf; a.gam = c->matdf + 3 * c->n; a.inv_mu = c->has_mu ? c->matdf + 3 * c->n + c->gam_len : nullptr;
+  a.kind = c->kind; a.ax_a = c->ax_a; a.ax_b = c->ax_b;
+  a.n1 = c->n1; a.n2 = c->n2; a.n3 = c->n3; a.alpha = nfs::df(c->opt.alpha); a.beta = nfs::df(c->opt.beta);
+  a.skip = skip; a.stream = c->stream;
+  a.basis = c->basisdf;
+  a.P = c->P;
+  a.bs = strides(c, 6 * c->n);
+  a.bs.sbasis = 6 * c->n;
+  return a;
+}
+
 // P products (problem p's vectors at u + p N); skip (optional): problem p is
 // skipped when skip[p * sskip] is nonzero.
 template <typename R>
@@ -210,7 +233,21 @@ int matvec(nfs_ctx* c, cudaStream_t s, const nfs::cplx<R>* u, nfs::cplx<R>* Au, 
   cudaError_t e = nfs::matvec_launch<R>(a);
   if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
   c->launches += 3;
-  if (sizeof(R) == 4) c->mv32 += c->P; else c->mv64 += c->P;
+  if (sizeof(nfs::cplx<R>) == 8) c->mv32 += c->P; else c->mv64 += c->P;
+  return NFS_OK;
+}
+
+// FP64-accuracy products of complex128 vectors through the double-single
+// product (mixed contexts): u is converted into the free CG direction buffer
+// p64, the result is written into out and converted there in place.
+int matvec_refine(nfs_ctx* c, cudaStream_t s, const double2* u, double2* out, const int* skip, int sskip) {
+  const long long reals = 2 * c->P * c->N;
+  nfs::dfc* uin = reinterpret_cast<nfs::dfc*>(c->p64);
+  nfs::dfc* res = reinterpret_cast<nfs::dfc*>(out);
+  CK(nfs::double_to_df(reinterpret_cast<const double*>(u), reinterpret_cast<nfs::df*>(uin), reals, s));
+  TRY(matvec<nfs::df>(c, s, uin, res, skip, sskip));
+  CK(nfs::df_to_double(reinterpret_cast<const nfs::df*>(res), reinterpret_cast<double*>(out), reals, s));
+  c->launches += 2;
   return NFS_OK;
 }
 
@@ -474,7 +511,7 @@ int solve(nfs_ctx* c, const double2* b, double2* x, bool x_zero, const std::vect
     // next residual: complex128 product of x, or complex64 product of d
     TRY(put_flags(c, s, 2 * P, skip64));
     TRY(put_flags(c, s, 3 * P, skip32));
-    if (any64) TRY(matvec<double>(c, s, x, c->Ap64, c->d_flags + 2 * P, 1));
+    if (any64) TRY(matvec_refine(c, s, x, c->Ap64, c->d_flags + 2 * P, 1));
     if (any32) TRY(matvec<float>(c, s, c->x32, c->Ap32, c->d_flags + 3 * P, 1));
     nfs::k_refine_residual<<<nb, 256, 0, s>>>(c->r64, b, c->Ap64, c->Ap32, c->d_small + 2 * P, c->d_flags + 2 * P,
                                               c->d_flags + 3 * P, c->N, tot);
@@ -914,7 +951,8 @@ void free_ctx(nfs_ctx* c) {
   if (!c) return;
   for (GraphEntry& g : c->graphs) cudaGraphExecDestroy(g.exec);
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
-                  c->mat64, c->mat32, c->basis64, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
+                  c->mat64, c->mat32, c->basis64, c->lamdf, c->twdf[0], c->twdf[1], c->twdf[2], c->matdf,
+                  c->basisdf, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
                   c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
                   c->MV32lo, c->dY};
   for (void* p : ptrs)
@@ -1149,6 +1187,21 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
   }
   TRYC(dalloc(c, &c->basis64, (size_t)P * 6 * c->n));
   CKC(nfs::basis_table_launch(c->lam64, n1, n2, n3, o.alpha, o.beta, c->basis64, P, nl, 6 * c->n, 0));
+  if (o.precision == NFS_PREC_MIXED) {
+    TRYC(dalloc(c, &c->lamdf, (size_t)P * nl));
+    CKC(nfs::double_to_df(reinterpret_cast<const double*>(c->lam64), reinterpret_cast<nfs::df*>(c->lamdf),
+                          2LL * P * nl, 0));
+    for (int l = 0; l < 3; ++l) {
+      TRYC(dalloc(c, &c->twdf[l], nn[l]));
+      CKC(nfs::double_to_df(reinterpret_cast<const double*>(c->tw64[l]), reinterpret_cast<nfs::df*>(c->twdf[l]),
+                            2LL * nn[l], 0));
+    }
+    TRYC(dalloc(c, &c->matdf, (size_t)P * c->mat_len));
+    CKC(nfs::double_to_df(c->mat64, c->matdf, (long long)P * c->mat_len, 0));
+    TRYC(dalloc(c, &c->basisdf, (size_t)P * 6 * c->n));
+    CKC(nfs::double_to_df(reinterpret_cast<const double*>(c->basis64), reinterpret_cast<nfs::df*>(c->basisdf),
+                          2LL * P * 6 * c->n, 0));
+  }
   const size_t PN = (size_t)P * c->N;
   TRYC(dalloc(c, (double2**)&c->fld, (size_t)P * 6 * c->n));
   TRYC(dalloc(c, &c->x64, PN));
@@ -1174,6 +1227,7 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
   TRYC(ensure_scratch(c, (size_t)kRedBlocks * 2 * 64 * P + 4096));
   CKC(nfs::matvec_prepare<double>(n1, n2, n3));
   CKC(nfs::matvec_prepare<float>(n1, n2, n3));
+  if (o.precision == NFS_PREC_MIXED) CKC(nfs::matvec_prepare<nfs::df>(n1, n2, n3));
   CKC(nfs::grad_prepare(n1, n2, n3));
   CKC(cudaDeviceSynchronize());
 #undef TRYC
@@ -1268,6 +1322,10 @@ extern "C" int nfs_matvec(nfs_ctx* c, int dtype, const void* u, void* Au) {
   if (((uintptr_t)u | (uintptr_t)Au) & 15) return NFS_EINVAL;  // 16-byte vector access
   if (dtype == NFS_C128) return matvec<double>(c, c->stream, (const double2*)u, (double2*)Au);
   if (dtype == NFS_C64) return matvec<float>(c, c->stream, (const float2*)u, (float2*)Au);
+  if (dtype == NFS_C128_DS) {
+    if (!c->lamdf) return NFS_EINVAL;  // FP64 contexts hold no double-single tables
+    return matvec_refine(c, c->stream, (const double2*)u, (double2*)Au, nullptr, 0);
+  }
   return NFS_EINVAL;
 }
 

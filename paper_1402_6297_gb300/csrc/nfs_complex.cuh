@@ -42,6 +42,12 @@ template <typename C> __host__ __device__ __forceinline__ typename RealOf<C>::ty
   return a.x * a.x + a.y * a.y;
 }
 
+// Read-only global loads of the element types (the double-single type adds
+// its own overload).
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ldg_c(const float4* p) { return __ldg(p); }
+
 #ifndef NFS_PACKED_F32
 #define NFS_PACKED_F32 1
 #endif

@@ -38,6 +38,7 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 C128 = 0
 C64 = 1
+C128_DS = 2
 
 EXPORTED = (
     "nfs_default_options", "nfs_setup", "nfs_matvec", "nfs_matvec_passes", "nfs_apply_Br", "nfs_cg_solve",
@@ -292,6 +293,16 @@ class Context:
         if out is None:
             out = torch.empty_like(u)
         _check(lib().nfs_matvec(self.h, code, self._vec(u, dt), self._vec(out, dt)), "nfs_matvec")
+        return out
+
+    def matvec_ds(self, u, out=None):
+        """A_r u for a complex128 tensor, computed in double-single arithmetic
+        (mixed contexts; the product their refinement residuals use)."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty_like(u)
+        _check(lib().nfs_matvec(self.h, C128_DS, self._vec(u, torch.complex128), self._vec(out, torch.complex128)),
+               "nfs_matvec")
         return out
 
     def matvec_passes(self, mask, u, out):

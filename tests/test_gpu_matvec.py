@@ -175,3 +175,22 @@ def test_matvec_full_size_128(nfs):
     got32 = ctx.matvec(torch.from_numpy(u.astype(np.complex64)).cuda()).cpu().numpy()
     assert rel_err(got32, ref) < 2e-5
     ctx.close()
+
+
+@pytest.mark.parametrize("grid", [(8, 8, 8), (12, 12, 16), (96, 96, 96), (128, 128, 128)])
+def test_matvec_double_single(nfs, grid):
+    """The double-single product (float pairs on the FP32 units) that the mixed
+    path uses for its refinement residuals: within 1e-12 of the oracle, like
+    the complex128 product, at three-pass and five-pass sizes."""
+    med = wl.smoothed_chiral_field(grid, seed=5, sigma=0.1)
+    ctx = nfs.Context(grid, K, med, precision="mixed")
+    orc = nfgep.NFGEP(grid, K, med)
+    u = wl.random_complex(4 * ctx.n, 41)
+    ref = orc.Ar(u)
+    got = ctx.matvec_ds(torch.from_numpy(u).cuda()).cpu().numpy()
+    assert rel_err(got, ref) < 1e-12
+    ctx.close()
+    ctx64 = nfs.Context(grid, K, med, precision="fp64")
+    with pytest.raises(nfs.NFSError):
+        ctx64.matvec_ds(torch.from_numpy(u).cuda())
+    ctx64.close()
