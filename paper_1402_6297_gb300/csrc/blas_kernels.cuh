@@ -18,7 +18,7 @@ namespace nfs {
 
 constexpr int kRedBlocks = 304;   // two blocks per SM on a 152-SM GB300
 constexpr int kRedThreads = 256;
-constexpr int kMaxPartials = 1024;  // >= 6 * n3 (pass-3 CTAs), kRedBlocks and kUpdBlocks
+constexpr int kMaxPartials = 2048;  // >= the product's p^* A p partials, kRedBlocks and kUpdBlocks
 constexpr int kUpdBlocks = 608;     // x/r update grid: four blocks of 512 per SM
 constexpr int kUpdThreads = 512;
 
@@ -33,7 +33,7 @@ struct CGState {
   int status;       // 0, -6 (no convergence) or -7 (breakdown)
   int npart_a;      // number of valid entries of part_a
   unsigned int arrived;  // blocks of the x/r update that have written their partial
-  double part_a[kMaxPartials];  // partials of p^* A p (written by pass 3 or k_dot_re)
+  double part_a[kMaxPartials];  // partials of p^* A p (written by the product or k_dot_re)
   double part_b[kMaxPartials];  // partials of r^* r
 };
 constexpr long long kStateDoubles = sizeof(CGState) / sizeof(double);

@@ -46,7 +46,7 @@ struct MatvecArgs {
   // CG fusion (both optional, nullptr when unused):
   const cplx<R>* cg_r;    // pass 1 first forms u = cg_r + (*cg_beta) u in place
   const double* cg_beta;
-  double* dot_part;       // pass 3 writes one partial of Re(u^* A u) per CTA
+  double* dot_part;       // one partial of Re(u^* A u) per CTA of pass 2 (pass 3b in the five-pass form)
   // batching: P problems of this grid in one launch (P = 1 for one problem)
   int P;
   BatchStrides bs;

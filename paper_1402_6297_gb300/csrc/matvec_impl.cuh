@@ -138,13 +138,16 @@ static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
           a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.basis, a.bs);
     } else {
       k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
-          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.u, a.dot_part, a.basis, a.bs);
+          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.basis, a.bs);
     }
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;
   }
 }
+
+template <typename R>
+static bool split_rt(int n);
 
 template <typename R, int N3>
 static cudaError_t z_launch(const MatvecArgs<R>& a) {
@@ -154,8 +157,8 @@ static cudaError_t z_launch(const MatvecArgs<R>& a) {
   MatView<R> mv{a.inv_phi, a.gam, a.inv_mu, a.kind, a.ax_a, a.ax_b, (long long)ncols * a.n3};
   const R inv_n = (R)(1.0 / ((double)ncols * (double)a.n3));
   k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))>
-      <<<(ncols / TX) * (a.P > 0 ? a.P : 1), NT, z_smem<R, N3>(), a.stream>>>(a.fld, mv, a.tw3, ncols, inv_n, a.skip,
-                                                                             a.bs);
+      <<<(ncols / TX) * (a.P > 0 ? a.P : 1), NT, z_smem<R, N3>(), a.stream>>>(
+          a.fld, mv, a.tw3, ncols, inv_n, a.skip, split_rt<R>(a.n1) ? nullptr : a.dot_part, a.bs);
   return cudaGetLastError();
 }
 
@@ -260,7 +263,7 @@ static bool split_rt(int n) {
 
 template <typename R>
 int matvec_dot_partials(int n1, int n2, int n3) {
-  return split_rt<R>(n1) ? (n2 / kSplitRows) * 2 * n3 : 6 * n3;
+  return split_rt<R>(n1) ? (n2 / kSplitRows) * 2 * n3 : (n1 * n2) / z_tile(n3, (int)sizeof(cplx<R>));
 }
 
 #define NFS_INSTANTIATE_MATVEC(R)                                            \

@@ -420,7 +420,7 @@ __device__ __forceinline__ void material_apply(const MatView<R>& m, long long v,
 template <typename R, int N3, int TX, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __restrict__ twz, int ncols,
-                   R inv_n, const int* __restrict__ skip, BatchStrides bs) {
+                   R inv_n, const int* __restrict__ skip, double* __restrict__ dot_part, BatchStrides bs) {
   using C = cplx<R>;
   constexpr int LINES = 6 * TX;
   constexpr int PITCH = LINES + 1;
@@ -445,6 +445,9 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
   __syncthreads();  // twiddles
   smem_fft_io<true, N3, LINES, NT, 1, PITCH, true, false>(buf, stw, [&](int l, int z) { return ldg_c(gaddr(l, z)); },
                                                          NoPut{});
+  // CG curvature from the real-space fields (Parseval; the DFTs carry the
+  // factor n that inv_n removes): u^* A_r u = sum Re(conj(P) f + conj(Q) w)
+  double dot_acc = 0.0;
   for (int idx = threadIdx.x; idx < N3 * TX; idx += NT) {
     const int c = idx % TX, z = idx / TX;
     C* row = buf + z * PITCH + c;
@@ -452,6 +455,13 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
     C q[3] = {row[3 * TX], row[4 * TX], row[5 * TX]};
     C fo[3], wo[3];
     material_apply<R>(mat, (long long)z * ncols + col0 + c, p, q, fo, wo, inv_n);
+    if (dot_part != nullptr) {
+      R sacc = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        sacc += p[k].x * fo[k].x + p[k].y * fo[k].y + q[k].x * wo[k].x + q[k].y * wo[k].y;
+      dot_acc += (double)sacc;
+    }
     row[0] = fo[0];
     row[TX] = fo[1];
     row[2 * TX] = fo[2];
@@ -459,7 +469,12 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
     row[4 * TX] = wo[1];
     row[5 * TX] = wo[2];
   }
-  __syncthreads();
+  if (dot_part != nullptr) {
+    const double tot = block_sum_dbl<NT>(dot_acc);  // (its barriers also order the material writes)
+    if (threadIdx.x == 0) dot_part[(long long)prob * bs.sstate + blockIdx.x % tiles] = tot;
+  } else {
+    __syncthreads();
+  }
   smem_fft_io<false, N3, LINES, NT, 1, PITCH, false, true>(buf, stw, NoGet{},
                                                           [&](int l, int z, C v) { *gaddr(l, z) = v; });
 }
@@ -472,8 +487,7 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au,
                        const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                        const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
-                       const int* __restrict__ skip, const cplx<R>* __restrict__ u, double* __restrict__ dot_part,
-                       const cplx<R>* __restrict__ basis, BatchStrides bs) {
+                       const int* __restrict__ skip, const cplx<R>* __restrict__ basis, BatchStrides bs) {
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
@@ -492,10 +506,6 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   Au += prob * bs.su;
   lam += (long long)prob * bs.slam;
   if (basis != nullptr) basis += prob * bs.sbasis;
-  if (dot_part != nullptr) {
-    u += prob * bs.su;
-    dot_part += prob * bs.sstate;
-  }
   for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
   const C* in = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
@@ -514,12 +524,9 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   C* o1 = o0 + n;
   const C a3 = lam[NX + NY + i3];
   const int e0 = third_bound<NE>(rank), e1 = third_bound<NE>(rank + 1);
-  double dot_acc = 0.0;
   using V = typename Lane<C>::V;
   V* o0v = reinterpret_cast<V*>(o0);
   V* o1v = reinterpret_cast<V*>(o1);
-  const C* u0 = u + (2 * grp) * n + (long long)i3 * NE;
-  const C* u1 = u0 + n;
   // EPV consecutive elements per lane (e0, e1 even)
   for (int ev = e0 / EPV + (int)threadIdx.x; ev < e1 / EPV; ev += NT) {
     C r0[EPV], r1[EPV];
@@ -548,20 +555,6 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
       o0v[ev] = r0[0];
       o1v[ev] = r1[0];
     }
-    if (dot_part != nullptr) {
-      // Re(u^* A u) over this CTA's outputs (the CG curvature p^* A p)
-      R sacc = 0;
-#pragma unroll
-      for (int h = 0; h < EPV; ++h) {
-        const C pa = u0[ev * EPV + h], pb = u1[ev * EPV + h];
-        sacc += pa.x * r0[h].x + pa.y * r0[h].y + pb.x * r1[h].x + pb.y * r1[h].y;
-      }
-      dot_acc += (double)sacc;
-    }
-  }
-  if (dot_part != nullptr) {
-    const double tot = block_sum_dbl<NT>(dot_acc);
-    if (threadIdx.x == 0) dot_part[((long long)i3 * 2 + blockIdx.y) * 3 + blockIdx.x] = tot;
   }
   cl.sync();  // keep this CTA's plane alive until the cluster finished reading it
 }
