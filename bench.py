@@ -180,6 +180,14 @@ def profiled_traffic(pass_index):
     return int(v) if v else None
 
 
+def cg_iteration_roofline(n, product_bytes, info, hbm):
+    vec = 4 * n * 8
+    b = product_bytes + 2 * vec + 6 * vec
+    us = 1e6 * info.seconds_cg / max(int(info.cg_iterations), 1)
+    gbps = b / (us * 1e-6) / 1e9
+    return {"bytes": b, "us": us, "GBps": gbps, "frac": gbps / hbm}
+
+
 def bytes_per_pass(n, csize, kind):
     """Algorithmic HBM bytes of each pass of one A_r product (3-pass model):
     pass 1 reads u (4n) and writes six fields (6n); pass 2 reads and writes the
@@ -493,6 +501,10 @@ def run_ours(args):
                    "grid": list(grid), "nev": NEV},
         "matvecs_per_s": {"c64": 1000.0 / mv64_ms, "c128": 1000.0 / mv128_ms},
         "cg_iters_per_s": cg_its / (statistics.mean(step_ms) / 1000.0),
+        # one complex64 CG iteration as implemented: the product (3-pass
+        # bytes) + pass 1 reading r and writing p + the x/r update reading x,
+        # r, p, A p and writing x, r (vectors of 4n complex64)
+        "cg_iteration": cg_iteration_roofline(n, sum(bpp), info, hbm),
         "eigensolve": {"lanczos_steps": info.lanczos_steps, "restarts": info.restarts,
                        "cg_iterations": int(cg_its), "matvecs_c64": int(info.matvecs_c64),
                        "matvecs_c128": int(info.matvecs_c128), "nconv": info.nconv,
