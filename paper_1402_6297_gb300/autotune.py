@@ -1,0 +1,152 @@
+"""Autotuner for the complex64 A_r product's kernel schedule.
+
+The schedule knobs are compile-time (template parameters of the pass
+kernels): the radix split N = N1 * N2 of each line length (NFS_N1_<N>), the
+z-pass tile width and thread count, the CTAs per SM requested for the plane
+and z passes, and one or two complex elements per lane.  This tool builds
+variants of libnfs.so with candidate settings (in parallel, in a scratch
+directory), times the complex64 product of each on seeded smoothed chiral
+fields of the requested grid sizes, checks each variant against the
+complex128 product, and improves the settings one knob at a time
+(coordinate descent from the current defaults).  The result is written to
+csrc/tuning.h, which every kernel header includes; rebuild afterwards.
+
+  python -m paper_1402_6297_gb300.autotune --sizes 48,64,96 [--rounds 1]
+
+Needs a GPU.  Each variant is a full build (a minute or two on 16 cores).
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+TUNING_H = os.path.join(HERE, "csrc", "tuning.h")
+
+# knob -> candidate values (the first is the built-in default)
+KNOBS = {
+    "NFS_N1_32": [8, 4, 16],
+    "NFS_N1_48": [8, 6, 12, 16],
+    "NFS_N1_64": [8, 16, 4],
+    "NFS_N1_96": [12, 8, 16, 6],
+    "NFS_N1_128": [16, 8],
+    "NFS_PLANE_MINB": [3, 2],
+    "NFS_Z_MINB": [3, 2],
+    "NFS_ZTILE_C64": [16, 8],
+    "NFS_C64_PAIRS": [0, 1],
+}
+# knobs that only matter for some sizes
+KNOB_SIZES = {"NFS_N1_32": {32}, "NFS_N1_48": {48}, "NFS_N1_64": {64}, "NFS_N1_96": {96}, "NFS_N1_128": {128}}
+
+
+def time_variant(lib, size, reps=30):
+    """Median complex64 product time (ms) for one library on one grid size,
+    and the product's relative distance from the complex128 one."""
+    code = f"""
+import sys, json, statistics
+sys.path.insert(0, {ROOT!r})
+import torch, numpy as np
+import workloads as wl
+from paper_1402_6297_gb300 import nfs
+nfs.LIB_PATH = {lib!r}
+g = ({size}, {size}, {size})
+ctx = nfs.Context(g, (0.1, 0.2, 0.3), wl.smoothed_chiral_field(g, seed=1), precision="mixed")
+n = g[0] * g[1] * g[2]
+u = torch.from_numpy(wl.random_complex(4 * n, 2)).cuda()
+ref = ctx.matvec(u)
+u32 = u.to(torch.complex64)
+out = ctx.matvec(u32)
+err = float((out.to(torch.complex128) - ref).abs().max() / ref.abs().max())
+flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+st = torch.cuda.current_stream()
+ts = []
+for _ in range({reps}):
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st); ctx.matvec(u32, out); e1.record(st)
+    torch.cuda.synchronize()
+    ts.append(e0.elapsed_time(e1))
+print(json.dumps({{"ms": statistics.median(ts), "err": err}}))
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    if r.returncode != 0:
+        print(json.dumps({"failed": lib, "size": size, "stderr": r.stderr[-600:]}), flush=True)
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def build_variant(defines, workdir):
+    from paper_1402_6297_gb300 import build
+    tag = "_".join(f"{k[4:]}{v}" for k, v in sorted(defines.items()))
+    d = os.path.join(workdir, tag)
+    lib = os.path.join(d, build.LIBNAME)
+    if os.path.exists(lib):  # built already in this run
+        return lib
+    return build.build(force=True, libdir=d, defines=[f"{k}={v}" for k, v in defines.items()])
+
+
+def score(defines, sizes, workdir, cache):
+    key = tuple(sorted(defines.items()))
+    if key in cache:
+        return cache[key]
+    try:
+        lib = build_variant(defines, workdir)
+    except RuntimeError:
+        cache[key] = None
+        return None
+    total, ok = 0.0, True
+    for s in sizes:
+        r = time_variant(lib, s)
+        if r is None or not (r["err"] < 2e-5):
+            ok = False
+            break
+        total += r["ms"] / s ** 3  # time per voxel: every size counts alike
+    cache[key] = total if ok else None
+    return cache[key]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--sizes", default="48,64,96")
+    ap.add_argument("--rounds", type=int, default=1)
+    ap.add_argument("--jobs", type=int, default=4, help="variants built in parallel")
+    args = ap.parse_args()
+    sizes = [int(x) for x in args.sizes.split(",")]
+    best = {k: v[0] for k, v in KNOBS.items()}
+    cache = {}
+    with tempfile.TemporaryDirectory(prefix="nfs_autotune_") as workdir:
+        base = score(best, sizes, workdir, cache)
+        print(json.dumps({"defaults": best, "score": base}), flush=True)
+        for _ in range(args.rounds):
+            for knob, values in KNOBS.items():
+                if knob in KNOB_SIZES and not (KNOB_SIZES[knob] & set(sizes)):
+                    continue
+                cands = [dict(best, **{knob: v}) for v in values if v != best[knob]]
+                with cf.ThreadPoolExecutor(max_workers=args.jobs) as ex:
+                    list(ex.map(lambda d: build_variant(d, workdir) if tuple(sorted(d.items())) not in cache else None,
+                                cands))
+                for cand in cands:
+                    sc = score(cand, sizes, workdir, cache)
+                    print(json.dumps({"try": {knob: cand[knob]}, "score": sc}), flush=True)
+                    if sc is not None and (base is None or sc < base * 0.99):
+                        best, base = cand, sc
+                print(json.dumps({"knob": knob, "chosen": best[knob], "score": base}), flush=True)
+    lines = ["// Written by autotune.py: the complex64 product's kernel schedule for this GPU",
+             f"// (grid sizes {args.sizes}; score = sum of product time per voxel).", "#pragma once"]
+    for k, v in best.items():
+        lines.append(f"#define {k} {v}")
+    with open(TUNING_H, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print(json.dumps({"tuning_h": TUNING_H, "chosen": best, "score": base}), flush=True)
+
+
+if __name__ == "__main__":
+    main()

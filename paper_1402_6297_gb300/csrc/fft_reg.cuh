@@ -144,16 +144,41 @@ struct DFT {
 };
 
 // Two-level split of a line length N = N1 * N2 used by the shared-memory
-// line FFT (see fft_smem.cuh).
+// line FFT (see fft_smem.cuh).  The first factor of each length is a tuning
+// choice (NFS_N1_<N>, picked by autotune.py into tuning.h); both factors must
+// be register DFT lengths (divisors of 48).
+#ifndef NFS_N1_24
+#define NFS_N1_24 6
+#endif
+#ifndef NFS_N1_32
+#define NFS_N1_32 8
+#endif
+#ifndef NFS_N1_48
+#define NFS_N1_48 8
+#endif
+#ifndef NFS_N1_64
+#define NFS_N1_64 8
+#endif
+#ifndef NFS_N1_96
+#define NFS_N1_96 12
+#endif
+#ifndef NFS_N1_128
+#define NFS_N1_128 16
+#endif
+template <int N, int F1>
+struct SplitOf {
+  static_assert(N % F1 == 0 && 48 % F1 == 0 && 48 % (N / F1) == 0, "line split factors must divide 48");
+  static constexpr int N1 = F1, N2 = N / F1;
+};
 template <int N> struct LineSplit;
 template <> struct LineSplit<8>   { static constexpr int N1 = 8,  N2 = 1; };
 template <> struct LineSplit<12>  { static constexpr int N1 = 12, N2 = 1; };
 template <> struct LineSplit<16>  { static constexpr int N1 = 16, N2 = 1; };
-template <> struct LineSplit<24>  { static constexpr int N1 = 6,  N2 = 4; };
-template <> struct LineSplit<32>  { static constexpr int N1 = 8,  N2 = 4; };
-template <> struct LineSplit<48>  { static constexpr int N1 = 8,  N2 = 6; };
-template <> struct LineSplit<64>  { static constexpr int N1 = 8,  N2 = 8; };
-template <> struct LineSplit<96>  { static constexpr int N1 = 12, N2 = 8; };
-template <> struct LineSplit<128> { static constexpr int N1 = 16, N2 = 8; };
+template <> struct LineSplit<24>  : SplitOf<24, NFS_N1_24> {};
+template <> struct LineSplit<32>  : SplitOf<32, NFS_N1_32> {};
+template <> struct LineSplit<48>  : SplitOf<48, NFS_N1_48> {};
+template <> struct LineSplit<64>  : SplitOf<64, NFS_N1_64> {};
+template <> struct LineSplit<96>  : SplitOf<96, NFS_N1_96> {};
+template <> struct LineSplit<128> : SplitOf<128, NFS_N1_128> {};
 
 }  // namespace nfs

@@ -4,6 +4,14 @@
 #pragma once
 #include <cuda_runtime.h>
 
+// Kernel schedule choices written by autotune.py (line-DFT splits, tiles,
+// CTAs per SM); every knob has a default where it is used.
+#if defined(__has_include)
+#if __has_include("tuning.h")
+#include "tuning.h"
+#endif
+#endif
+
 namespace nfs {
 
 template <typename R> struct CplxOf;
