@@ -27,10 +27,13 @@ def test_tuning_header_uses_known_knobs():
     path = autotune.TUNING_H
     if not os.path.exists(path):
         pytest.skip("no tuning.h")
-    for line in open(path):
+    lines = open(path).read().splitlines()
+    for i, line in enumerate(lines):
         if line.startswith("#define"):
             _, name, value = line.split()
             assert name in autotune.KNOBS and int(value) in autotune.KNOBS[name], line
+            # guarded so that command-line settings (the autotuner's variants) win
+            assert lines[i - 1] == f"#ifndef {name}", line
 
 
 def test_reference_arm_prints_the_contract_line():
