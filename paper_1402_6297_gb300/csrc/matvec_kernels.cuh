@@ -5,10 +5,17 @@
 //           p^ = P_r-coefficients, q^ = Q_r-coefficients per voxel, then the
 //           inverse DFT along x and y.  Group 0 builds p = P_r [u1a; u1b],
 //           group 1 builds q = Q_r [u2a; u2b]; CTA rank c owns component c.
+//           Each CTA assembles all three components of its third of the
+//           plane and the CTAs exchange them through shared memory (Stage).
 //   pass 2  (one CTA per tile of xy columns):  inverse DFT along z, the
-//           per-voxel material product of eq. factor_mtx, forward DFT along z.
+//           per-voxel material product of eq. factor_mtx, forward DFT along z
+//           (the tile goes between global memory and registers directly).
 //   pass 3  (cluster of 3 CTAs per (z-plane, group)):  forward DFT along y
-//           and x, then the projections P_r^* f (group 0) or Q_r^* w (group 1).
+//           and x, then the projections P_r^* f (group 0) or Q_r^* w (group 1)
+//           from the three transformed components (remote shared loads).
+//
+// Planes too large for shared memory take the five-pass form of
+// matvec_split.cuh.
 //
 // Basis per spectral voxel (Section 2), with a = (Lambda_1, Lambda_2, Lambda_3),
 // t = (alpha, beta, 1), Lambda_p = t x a, Lambda_q = |a|^2:

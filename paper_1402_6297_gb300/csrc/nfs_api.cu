@@ -310,8 +310,9 @@ int put_flags(nfs_ctx* c, cudaStream_t s, int off, const std::vector<int>& v) {
 constexpr int kCgChunk = 8;
 
 // Enqueue kCgChunk iterations for all problems: pass 1 (which first forms
-// p = r + beta p), passes 2 and 3 (pass 3 also emits the p^* A p partials)
-// and the x/r update (which forms alpha, and in its last block beta).
+// p = r + beta p), passes 2 and 3 (pass 2 also emits the p^* A p partials,
+// from the real-space fields) and the x/r update (which forms alpha, and in
+// its last block beta).
 template <typename R>
 cudaError_t enqueue_cg_chunk(nfs_ctx* c, cudaStream_t s, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p,
                              nfs::cplx<R>* Ap) {
