@@ -98,3 +98,22 @@ def test_batch_of_one_equals_context(nfs):
     ref, _, _ = ctx.eigs(10, vectors=False)
     ctx.close()
     assert np.abs(omega[0] - ref).max() / ref.min() < 1e-12
+
+
+def test_batch_with_restarts_equals_single_contexts(nfs):
+    """A small basis (ncv 30 for nev 10) forces thick restarts; problems that
+    restart in lock-step inside a batch must give what each gives alone with
+    the same basis size."""
+    g = (16, 16, 16)
+    ks = wl.bz_path_midpoints(9)
+    probs = [(g, tuple(ks[j]), _sphere(g, 0.3 + 0.1 * j)) for j in (1, 4, 7)]
+    nev = 10
+    with nfs.Batch(probs, precision="mixed", ncv=30) as b:
+        omega, infos = b.eigs(nev)
+    assert max(i.restarts for i in infos) > 0
+    for i, (gg, k, med) in enumerate(probs):
+        ctx = nfs.Context(gg, k, med, precision="mixed", ncv=30)
+        ref, _, info = ctx.eigs(nev, vectors=False)
+        ctx.close()
+        assert info.restarts == infos[i].restarts
+        assert np.abs((omega[i] - ref) / ref).max() < 1e-12, (i, omega[i], ref)
