@@ -24,8 +24,8 @@
  * Ownership: a context copies everything it needs from the caller at setup
  * and owns all device workspaces; vector arguments are caller-owned DEVICE
  * pointers, used on the context's stream, never retained after a call
- * returns.  No call allocates device memory except nfs_setup and the first
- * nfs_eigs with a larger basis than any before.
+ * returns.  No call allocates device memory except nfs_setup, nfs_setup_batch
+ * and the first nfs_eigs / nfs_eigs_batch with a larger basis than any before.
  *
  * Errors: every int-returning call returns NFS_OK (0) or a negative NFS_E*
  * code; no C++ exception crosses the ABI.  nfs_strerror gives a message.
@@ -43,9 +43,8 @@ extern "C" {
 /* ---- error codes -------------------------------------------------------- */
 #define NFS_OK            0
 #define NFS_EINVAL       (-1)   /* bad pointer, size, option or enum             */
-#define NFS_EUNSUPPORTED (-2)   /* non-orthogonal lattice, or a grid size that   */
-                                /* is not one of 8,12,16,24,32,48,64,96,128 or   */
-                                /* whose xy plane exceeds shared memory          */
+#define NFS_EUNSUPPORTED (-2)   /* non-orthogonal lattice, n1 != n2, or a grid   */
+                                /* size not one of 8,12,16,24,32,48,64,96,128    */
 #define NFS_EKPOINT      (-3)   /* every k.a_l integer: Lambda_q singular (Lemma) */
 #define NFS_EBASIS       (-4)   /* alpha, beta violate the Lemma: Lambda_p = 0    */
 #define NFS_ENOTHPD      (-5)   /* mu <= 0 or Phi <= 0: Assumption (eq. assump)   */
@@ -60,7 +59,8 @@ extern "C" {
 #define NFS_MEDIUM_PSEUDOCHIRAL 1  /* xi_d = i gamma on the (axis_a, axis_b) pair only   */
 
 #define NFS_PREC_FP64  0  /* complex128 matvec, CG and Lanczos                    */
-#define NFS_PREC_MIXED 1  /* complex64 matvec + CG, FP64 refinement and Lanczos   */
+#define NFS_PREC_MIXED 1  /* complex64 matvec + CG; refinement residuals with the
+                           * double-single product; FP64 Lanczos                 */
 
 #define NFS_C128 0        /* vector element type: double2                         */
 #define NFS_C64  1        /* vector element type: float2                          */
@@ -152,15 +152,20 @@ int nfs_setup(nfs_ctx** out, const int grid[3], const double* lattice, const dou
               const nfs_material* mat, const nfs_options* opt);
 
 /* Au = A_r u (eq. factor_mtx / eq. spd_LS) in the given element type.  u and
- * Au are device pointers to 4n complex numbers and must not overlap. */
+ * Au are device pointers to 4n complex numbers and must not overlap.
+ * NFS_C128_DS: complex128 vectors, product in double-single arithmetic (~1e-14;
+ * MIXED contexts only, else NFS_EINVAL); it uses the context's CG workspace,
+ * so it must not overlap an nfs_cg_solve or nfs_eigs on the same context. */
 int nfs_matvec(nfs_ctx* ctx, int dtype, const void* u, void* Au);
 
 /* Run only the passes of nfs_matvec selected by `mask` (bit 0: pass 1,
  * spectral assembly + inverse DFT along x, y; bit 1: pass 2, inverse DFT
  * along z + material product + forward DFT along z; bit 2: pass 3, forward
- * DFT along y, x + projection onto P_r^*, Q_r^*).  Passes communicate through
- * the context's field workspace, so mask 7 equals nfs_matvec; other masks
- * exist to time the passes one by one.  Same arguments as nfs_matvec. */
+ * DFT along y, x + projection onto P_r^*, Q_r^*; where the xy plane does not
+ * fit in shared memory -- complex128 at 128 -- passes 1 and 3 are two kernels
+ * each).  Passes communicate through the context's field workspace, so mask 7
+ * equals nfs_matvec; other masks exist to time the passes one by one.  Same
+ * arguments as nfs_matvec (NFS_C128 and NFS_C64 only). */
 int nfs_matvec_passes(nfs_ctx* ctx, int dtype, int mask, const void* u, void* Au);
 
 /* out = B_r v = i [Sigma_r^{-1} v2; -Sigma_r^{-1} v1] (eq. NFSEP_spd_1), with
@@ -169,14 +174,18 @@ int nfs_apply_Br(nfs_ctx* ctx, const void* v, void* out);
 
 /* Solve A_r x = b by unpreconditioned CG (Section 4.2).  b, x: device
  * complex128 (4n); x holds the initial guess on entry.  FP64 contexts run CG
- * in complex128; MIXED contexts run complex64 CG inside FP64 iterative
- * refinement.  info may be NULL. */
+ * in complex128; MIXED contexts run complex64 CG inside iterative refinement
+ * whose residuals b - A_r x come from the double-single product, or, once the
+ * residual is below 2.5e4 cg_tol |b|, from the complex64 product of the small
+ * correction.  info may be NULL. */
 int nfs_cg_solve(nfs_ctx* ctx, const void* b, void* x, nfs_solve_info* info);
 
 /* The nev smallest positive eigenvalues omega of the GEP (eq.
  * discrete_GEP_EH), by thick-restart invert Lanczos on the HHPD-NFGEP: the
- * nev largest theta = 1/omega of B_r y = theta A_r y, orthogonalised in the
- * A_r inner product in FP64.  omega: HOST array of nev doubles, ascending.
+ * nev largest theta = 1/omega of B_r y = theta A_r y.  The basis is FP64 and
+ * A_r-orthogonal: FP64 three-term recurrence, and every step the inner
+ * products with all older vectors in double-single arithmetic, removing them
+ * when they exceed opt.orth_tol.  omega: HOST array of nev doubles, ascending.
  * Y: device complex128 array [nev][4n] of A_r-normalised eigenvectors y, or
  * NULL.  info may be NULL.  Returns NFS_ENOCONV (results still written) if the
  * restart cap is hit first. */
