@@ -282,14 +282,6 @@ __global__ void k_axpy_promote(double2* __restrict__ x, const double* __restrict
   }
 }
 
-// a *= s[problem]
-template <typename C>
-__global__ void k_scale(C* __restrict__ a, const double* __restrict__ s, long long N, long long total) {
-  using R = typename RealOf<C>::type;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-    a[i] = cscale(a[i], (R)s[i / N]);
-}
-
 // B_r v = i [Sigma^{-1} v2 ; -Sigma^{-1} v1], Sigma_r = diag(sqrt(Lq), sqrt(Lq))
 // (eq. NFSEP_spd_1).  lam holds Lambda_1 | Lambda_2 | Lambda_3 per problem
 // (stride n1 + n2 + n3); v and out hold P vectors of 4n.

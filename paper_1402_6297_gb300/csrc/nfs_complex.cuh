@@ -29,7 +29,6 @@ __host__ __device__ __forceinline__ double2 mk(double a, double b) { return make
 template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
 template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
 template <typename C> __host__ __device__ __forceinline__ C cneg(C a) { return mk(-a.x, -a.y); }
-template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
 template <typename C, typename R> __host__ __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
 // a * b
 template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
@@ -38,10 +37,6 @@ template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
 // conj(a) * b
 template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {
   return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
-}
-// acc + a * b
-template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C acc) {
-  return mk(acc.x + a.x * b.x - a.y * b.y, acc.y + a.x * b.y + a.y * b.x);
 }
 // i * a, -i * a
 template <typename C> __host__ __device__ __forceinline__ C cmul_i(C a) { return mk(-a.y, a.x); }
