@@ -23,7 +23,10 @@ media"):
   equivalent Hermitian-definite pencil; eigenvalue gradients.
 * :mod:`oracle.nfgep` -- Sections 4.1-4.2: the HHPD-NFGEP (thm:NFSEP_real_ew),
   the factored A_r (eq. (factor_mtx)) applied with FFTs (tier O3), B_r, CG
-  (eq. (spd_LS)) and an ARPACK invert-Lanczos eigensolve.
+  (eq. (spd_LS)), an ARPACK invert-Lanczos eigensolve, and the fields
+  x = [E; H] = B^{-1} diag(P_r, Q_r) y of Algorithm 1's final step; with
+  :func:`oracle.gep.gep_residual`, the relative residual of (omega, x) in the
+  GEP itself.
 
 Readings of the paper that the oracle fixes (the paper is silent or misprints):
 

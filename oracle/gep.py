@@ -39,6 +39,16 @@ def gep_matrices(grid, kdota, medium, a=1.0):
     return L, B
 
 
+def gep_residual(grid, kdota, medium, omega, x, a=1.0):
+    """Relative residual of an eigenpair (omega, x = [E; H]) of eq.
+    (discrete_GEP_EH): ||diag(C, C^*) x - omega B x|| / (|omega| ||B x||), with
+    the curl C assembled from its finite-difference blocks (eq. (mtx_C))."""
+    L, B = gep_matrices(grid, kdota, medium, a)
+    x = np.asarray(x, np.complex128).ravel()
+    Bx = B @ x
+    return float(np.linalg.norm(L @ x - omega * Bx) / (abs(omega) * np.linalg.norm(Bx)))
+
+
 def pencil_matrices(grid, kdota, medium, a=1.0):
     """(K'', B'') of the Hermitian-definite pencil described in the module docstring."""
     C = yee.curl_matrix(grid, kdota, a)

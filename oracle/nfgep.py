@@ -142,6 +142,22 @@ class NFGEP:
         omega = 1.0 / theta[order]
         return omega, Y[:, order]
 
+    # -- Algorithm 1, last step: the fields of the GEP -----------------------
+    def eigvec_fields(self, y):
+        """x = [E; H] = B^{-1} diag(P_r, Q_r) y (Algorithm 1, final step), with
+        B = i [[zeta_d, mu_d], [-eps_d, -xi_d]] of eq. (mtx_B).  B couples only
+        the six components of one voxel index, so B x = [P_r y1; Q_r y2] is
+        solved as one 6 x 6 system per voxel.  Returns (6, n3, n2, n1):
+        E_x, E_y, E_z, H_x, H_y, H_z."""
+        p, q = self.fields(y)
+        eps, mu, xi, zeta = om.tensors(self.medium)
+        B = 1j * np.concatenate([np.concatenate([zeta, mu], axis=1),
+                                 np.concatenate([-eps, -xi], axis=1)], axis=0)   # (6, 6, n3, n2, n1)
+        Bv = np.moveaxis(B.reshape(6, 6, self.n), -1, 0)                         # (n, 6, 6)
+        rhs = np.concatenate([p, q]).reshape(6, self.n).T                       # (n, 6)
+        x = np.linalg.solve(Bv, rhs[..., None])[..., 0]
+        return x.T.reshape((6,) + self.shape)
+
     def residual(self, omega, y):
         """||A_r y - omega B_r y|| / ||y||  (scale-free)."""
         return np.linalg.norm(self.Ar(y) - omega * self.Br(y)) / np.linalg.norm(y)
