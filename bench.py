@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-batch", action="store_true", help="skip the batched band-structure (bz48) leg")
     p.add_argument("--skip-grad", action="store_true", help="skip the eigenvalue-gradient (field64) leg")
+    p.add_argument("--skip-fields", action="store_true",
+                   help="skip the eigenvector-fields leg (E, H of the headline eigenpairs and their GEP residuals)")
     p.add_argument("--matvec-only", action="store_true",
                    help="time only the A_r products (profiling aid; prints a reduced line)")
     return p.parse_args()
@@ -343,6 +345,36 @@ def grad_leg(nfs, wl, torch, np):
             "grad_norm_eps": float(d_eps.norm()), "grad_norm_gamma": float(d_gam.norm())}
 
 
+def fields_leg(ctx, omega, Y, n, torch, hbm):
+    """Algorithm 1's final step on the headline eigenpairs: the fields
+    [E; H] = B^{-1} diag(P_r, Q_r) y of all NEV eigenvectors (nfs_eig_fields,
+    FP64) and their residuals in the 6n GEP (nfs_gep_residual)."""
+    stream = torch.cuda.current_stream()
+    m = int(Y.shape[0])
+    X = ctx.eig_fields(Y)  # warm
+    ms = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.eig_fields(Y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    res = ctx.gep_residual(omega, X)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = ctx.gep_residual(omega, X)
+    res_ms = 1000.0 * (time.perf_counter() - t0)
+    per_vec = statistics.median(ms) / m
+    # algorithmic bytes per vector (complex128): pass 1 reads y (4n) and
+    # writes 6n fields; the z pass reads them with the material (3 reals of
+    # 1/Phi, one gamma) and writes X (6n)
+    fbytes = n * (4 * 16 + 6 * 16 + 6 * 16 + 4 * 8 + 6 * 16)
+    return {"vectors": m, "fields_ms_per_vector": per_vec,
+            "fields_GBps": fbytes / (per_vec / 1e3) / 1e9, "fields_frac": fbytes / (per_vec / 1e3) / 1e9 / hbm,
+            "residual_ms_per_vector": res_ms / m, "max_gep_residual": float(max(res))}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
@@ -485,6 +517,7 @@ def run_ours(args):
     h2d = pin_eps.numel() * 8 + pin_gam.numel() * 8
     d2h = NEV * 8
 
+    fields = None if (args.skip_fields or rank != 0) else fields_leg(ctx, omega, Y, n, torch, hbm)
     # the secondary legs get the device memory of the headline context
     ctx.close()
     batch = None if (args.skip_batch or rank != 0) else batch_leg(nfs, wl, torch)
@@ -524,6 +557,7 @@ def run_ours(args):
         "fp64": fp64,
         "batch": batch,
         "gradient": grad,
+        "fields": fields,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

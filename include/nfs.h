@@ -204,6 +204,28 @@ int nfs_eigs(nfs_ctx* ctx, int nev, double* omega, void* Y, nfs_eigs_info* info)
 int nfs_eig_grad(nfs_ctx* ctx, int m, const double* weights, const void* Y,
                  double* d_eps, double* d_gamma);
 
+/* Fields of eigenvectors (Algorithm 1, final step):
+ *   x_j = [E; H] = B^{-1} diag(P_r, Q_r) y_j,  B = i [[zeta_d, mu_d], [-eps_d, -xi_d]]
+ * (eq. mtx_B).  For an eigenpair (omega, y) of the HHPD-NFGEP, (omega, x) is
+ * an eigenpair of the GEP diag(C, C^*) x = omega B x (eq. discrete_GEP_EH),
+ * Bloch twist included: E and H are the fields on the Yee grid themselves.
+ *   Y: DEVICE complex128 [m][4n] (e.g. from nfs_eigs), any scaling.
+ *   X: DEVICE complex128 [m][6][n3][n2][n1], components E_x, E_y, E_z, H_x,
+ *      H_y, H_z.
+ * Both 16-byte aligned.  Computed in FP64 on every context; stream-ordered on
+ * opt.stream (no host synchronisation).  Single-problem contexts only
+ * (NFS_EUNSUPPORTED for the classes of a batch). */
+int nfs_eig_fields(nfs_ctx* ctx, int m, const void* Y, void* X);
+
+/* Relative residuals of eigenpairs of the GEP (eq. discrete_GEP_EH):
+ *   res[j] = ||diag(C, C^*) x_j - omega_j B x_j||_2 / (|omega_j| ||B x_j||_2),
+ * with the Yee curl C applied as its finite-difference stencil (eqs. mtx_C,
+ * mtx_C123, mtx_K_n1), independent of the FFT factorisation.
+ *   omega: HOST, m nonzero doubles.  X: DEVICE complex128 [m][6n] as written
+ *   by nfs_eig_fields.  res: HOST, m doubles.
+ * Synchronises opt.stream.  Single-problem contexts only. */
+int nfs_gep_residual(nfs_ctx* ctx, int m, const double* omega, const void* X, double* res);
+
 /* ---- allocation-free product ------------------------------------------ */
 
 /* Largest voxel count n1*n2*n3 that nfs_matvec_noalloc accepts (32^3). */

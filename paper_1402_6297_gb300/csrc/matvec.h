@@ -96,4 +96,36 @@ struct GradArgs {
 cudaError_t grad_prepare(int n1, int n2, int n3);
 cudaError_t grad_launch(const GradArgs& a);
 
+// Fields [E; H] = B^{-1} diag(P_r, Q_r) y of one eigenvector from the pass-1
+// fields of y (matvec_f64.cu).
+struct FieldsArgs {
+  const double2* fld;     // pass-1 output, 6n
+  const double2* tw3;
+  const double2* bloch;   // D_1 | D_2 | D_3 diagonals, n1 + n2 + n3
+  const double* inv_phi;
+  const double* gam;
+  const double* inv_mu;   // nullptr for mu = 1
+  int kind, ax_a, ax_b;
+  int n1, n2, n3;
+  double2* X;             // 6n out: E_x, E_y, E_z, H_x, H_y, H_z
+  cudaStream_t stream;
+};
+cudaError_t fields_prepare(int n1, int n2, int n3);
+cudaError_t fields_launch(const FieldsArgs& a);
+
+// Partial sums of the GEP residual of (omega, x) (matvec_f64.cu).
+struct GepResidualArgs {
+  const double2* X;       // 6n: E_x, E_y, E_z, H_x, H_y, H_z
+  const double* inv_phi;
+  const double* gam;
+  const double* inv_mu;   // nullptr for mu = 1
+  int kind, ax_a, ax_b;
+  int n1, n2, n3;
+  double inv_delta[3];
+  double2 wrap[3];        // exp(i 2 pi k.a_l)
+  double omega;
+  double* part;           // 2 per block: |residual|^2, |B x|^2
+};
+cudaError_t gep_residual_launch(const GepResidualArgs& a, int blocks, cudaStream_t stream);
+
 }  // namespace nfs

@@ -63,6 +63,10 @@ struct nfs_ctx {
   double* mat64 = nullptr;
   float* mat32 = nullptr;
   double2* basis64 = nullptr;  // per problem [6][n]: c and x of every voxel (complex128 products)
+  // Bloch twist of T (eq. mtx_T), per problem (stride nl): the diagonals
+  // D_l[j] = exp(i 2 pi k.a_l j / n_l), l = 1, 2, 3; and k.a_l itself
+  double2* bloch64 = nullptr;
+  std::vector<double> kd;
   // double-single copies of the tables, material and basis (mixed contexts:
   // the refinement residual products)
   nfs::dfc* lamdf = nullptr;
@@ -952,7 +956,7 @@ void free_ctx(nfs_ctx* c) {
   if (!c) return;
   for (GraphEntry& g : c->graphs) cudaGraphExecDestroy(g.exec);
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
-                  c->mat64, c->mat32, c->basis64, c->lamdf, c->twdf[0], c->twdf[1], c->twdf[2], c->matdf,
+                  c->mat64, c->mat32, c->basis64, c->bloch64, c->lamdf, c->twdf[0], c->twdf[1], c->twdf[2], c->matdf,
                   c->basisdf, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
                   c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
                   c->MV32lo, c->dY};
@@ -1186,6 +1190,20 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
       CKC(cudaMemcpy(c->mat32 + (size_t)p * ml, m32.data(), ml * sizeof(float), cudaMemcpyHostToDevice));
     }
   }
+  {
+    std::vector<double2> d((size_t)P * nl);
+    c->kd.assign((size_t)3 * P, 0.0);
+    for (int p = 0; p < P; ++p)
+      for (int l = 0, off = 0; l < 3; off += nn[l], ++l) {
+        c->kd[3 * p + l] = prep[p].kd[l];
+        for (int j = 0; j < nn[l]; ++j) {
+          const double th = 2.0 * M_PI * prep[p].kd[l] * j / nn[l];
+          d[(size_t)p * nl + off + j] = make_double2(std::cos(th), std::sin(th));
+        }
+      }
+    TRYC(dalloc(c, &c->bloch64, (size_t)P * nl));
+    CKC(cudaMemcpy(c->bloch64, d.data(), d.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  }
   TRYC(dalloc(c, &c->basis64, (size_t)P * 6 * c->n));
   CKC(nfs::basis_table_launch(c->lam64, n1, n2, n3, o.alpha, o.beta, c->basis64, P, nl, 6 * c->n, 0));
   if (o.precision == NFS_PREC_MIXED) {
@@ -1230,6 +1248,7 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
   CKC(nfs::matvec_prepare<float>(n1, n2, n3));
   if (o.precision == NFS_PREC_MIXED) CKC(nfs::matvec_prepare<nfs::df>(n1, n2, n3));
   CKC(nfs::grad_prepare(n1, n2, n3));
+  CKC(nfs::fields_prepare(n1, n2, n3));
   CKC(cudaDeviceSynchronize());
 #undef TRYC
 #undef CKC
@@ -1414,6 +1433,69 @@ extern "C" int nfs_eig_grad(nfs_ctx* c, int m, const double* weights, const void
     if (e != cudaSuccess) return cuda_fail(e, "grad launch");
   }
   CK(cudaStreamSynchronize(s));
+  return NFS_OK;
+}
+
+extern "C" int nfs_eig_fields(nfs_ctx* c, int m, const void* Yv, void* Xv) {
+  if (!c || m <= 0 || !Yv || !Xv) return NFS_EINVAL;
+  if ((((uintptr_t)Yv) | ((uintptr_t)Xv)) & 15) return NFS_EINVAL;
+  if (c->P != 1) return NFS_EUNSUPPORTED;
+  const long long n = c->n, N = c->N;
+  const double2* Y = (const double2*)Yv;
+  double2* X = (double2*)Xv;
+  for (int j = 0; j < m; ++j) {
+    // pass 1 of the complex128 product: the sqrt(n)-scaled untwisted (p, q),
+    // transformed along x and y
+    nfs::MatvecArgs<double> a = margs<double>(c, Y + (long long)j * N, nullptr, nullptr);
+    cudaError_t e = nfs::pass1_launch<double>(a);
+    if (e != cudaSuccess) return cuda_fail(e, "fields pass 1");
+    nfs::FieldsArgs f{};
+    f.fld = (const double2*)c->fld; f.tw3 = c->tw64[2]; f.bloch = c->bloch64;
+    f.inv_phi = a.inv_phi; f.gam = a.gam; f.inv_mu = a.inv_mu;
+    f.kind = c->kind; f.ax_a = c->ax_a; f.ax_b = c->ax_b;
+    f.n1 = c->n1; f.n2 = c->n2; f.n3 = c->n3;
+    f.X = X + (long long)j * 6 * n; f.stream = c->stream;
+    e = nfs::fields_launch(f);
+    if (e != cudaSuccess) return cuda_fail(e, "fields launch");
+    c->launches += 2;
+  }
+  return NFS_OK;
+}
+
+extern "C" int nfs_gep_residual(nfs_ctx* c, int m, const double* omega, const void* Xv, double* res) {
+  if (!c || m <= 0 || !omega || !Xv || !res) return NFS_EINVAL;
+  if (c->P != 1) return NFS_EUNSUPPORTED;
+  for (int j = 0; j < m; ++j)
+    if (!(std::isfinite(omega[j]) && omega[j] != 0.0)) return NFS_EINVAL;
+  const long long n = c->n;
+  nfs::GepResidualArgs g{};
+  g.inv_phi = c->mat64; g.gam = c->mat64 + 3 * n;
+  g.inv_mu = c->has_mu ? c->mat64 + 3 * n + c->gam_len : nullptr;
+  g.kind = c->kind; g.ax_a = c->ax_a; g.ax_b = c->ax_b;
+  g.n1 = c->n1; g.n2 = c->n2; g.n3 = c->n3;
+  for (int l = 0; l < 3; ++l) {
+    g.inv_delta[l] = 1.0 / c->delta[l];
+    const double th = 2.0 * M_PI * c->kd[l];
+    g.wrap[l] = make_double2(std::cos(th), std::sin(th));
+  }
+  g.part = c->dscratch;
+  const int blocks = (int)std::min<long long>(kRedBlocks, (n + 255) / 256);
+  for (int j = 0; j < m; ++j) {
+    g.X = (const double2*)Xv + (long long)j * 6 * n;
+    g.omega = omega[j];
+    cudaError_t e = nfs::gep_residual_launch(g, blocks, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "GEP residual launch");
+    c->launches += 1;
+    CK(cudaMemcpyAsync(c->hscratch, c->dscratch, (size_t)2 * blocks * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double r2 = 0.0, b2 = 0.0;
+    for (int i = 0; i < blocks; ++i) {
+      r2 += c->hscratch[2 * i];
+      b2 += c->hscratch[2 * i + 1];
+    }
+    res[j] = std::sqrt(r2) / (std::fabs(omega[j]) * std::sqrt(b2));
+  }
   return NFS_OK;
 }
 

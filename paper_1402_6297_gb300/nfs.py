@@ -157,6 +157,10 @@ def lib():
     L.nfs_eigs.restype = ip
     L.nfs_eig_grad.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, vp, vp]
     L.nfs_eig_grad.restype = ip
+    L.nfs_eig_fields.argtypes = [vp, ip, vp, vp]
+    L.nfs_eig_fields.restype = ip
+    L.nfs_gep_residual.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(ctypes.c_double)]
+    L.nfs_gep_residual.restype = ip
     L.nfs_num_voxels.argtypes = [vp]
     L.nfs_num_voxels.restype = ctypes.c_longlong
     L.nfs_device_bytes.argtypes = [vp]
@@ -358,6 +362,35 @@ class Context:
                                   ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_gam.data_ptr())),
                "nfs_eig_grad")
         return d_eps, d_gam
+
+    def eig_fields(self, Y):
+        """Fields [E; H] = B^{-1} diag(P_r, Q_r) y of eigenvectors Y (m, 4n):
+        a CUDA complex128 tensor (m, 6, n3, n2, n1), components E_x, E_y, E_z,
+        H_x, H_y, H_z (nfs_eig_fields)."""
+        torch = self._torch
+        Y = Y.reshape(-1, self.N)
+        if not (Y.is_cuda and Y.dtype == torch.complex128 and Y.is_contiguous()):
+            raise ValueError("Y must be a contiguous CUDA complex128 tensor (m, 4n)")
+        m = int(Y.shape[0])
+        n1, n2, n3 = self.grid
+        X = torch.empty((m, 6, n3, n2, n1), dtype=torch.complex128, device="cuda")
+        _check(lib().nfs_eig_fields(self.h, m, ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(X.data_ptr())),
+               "nfs_eig_fields")
+        return X
+
+    def gep_residual(self, omega, X):
+        """||diag(C, C^*) x - omega B x|| / (|omega| ||B x||) per eigenpair of
+        the GEP, from fields X (m, 6n) (nfs_gep_residual)."""
+        torch = self._torch
+        X = X.reshape(-1, 6 * self.n)
+        if not (X.is_cuda and X.dtype == torch.complex128 and X.is_contiguous()):
+            raise ValueError("X must be a contiguous CUDA complex128 tensor (m, 6n)")
+        m = int(X.shape[0])
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).reshape(m))
+        res = np.zeros(m, dtype=np.float64)
+        _check(lib().nfs_gep_residual(self.h, m, _dptr(om), ctypes.c_void_p(X.data_ptr()), _dptr(res)),
+               "nfs_gep_residual")
+        return res
 
 
 class Batch:
