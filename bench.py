@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-batch", action="store_true", help="skip the batched band-structure (bz48) leg")
     p.add_argument("--skip-grad", action="store_true", help="skip the eigenvalue-gradient (field64) leg")
+    p.add_argument("--skip-bands", action="store_true", help="skip the band-structure (bands48) leg")
+    p.add_argument("--skip-mesh", action="store_true", help="skip the mesh-convergence (8^3 .. 128^3) leg")
     p.add_argument("--skip-fields", action="store_true",
                    help="skip the eigenvector-fields leg (E, H of the headline eigenpairs and their GEP residuals)")
     p.add_argument("--matvec-only", action="store_true",
@@ -345,6 +347,46 @@ def grad_leg(nfs, wl, torch, np):
             "grad_norm_eps": float(d_eps.norm()), "grad_norm_gamma": float(d_gam.norm())}
 
 
+def bands_leg(nfs, wl, torch):
+    """bands48: the band-structure sweep of Section 5.3 on a 48^3 grid: the
+    chiral sphere (eps_i, eps_o, gamma) = (13, 1, 0.5), 40 k-points along
+    G-X-M-R-G (10 per segment), the 10 smallest positive omega at each
+    (nfs_band_structure, mixed precision)."""
+    g = (48, 48, 48)
+    med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+    ks, _ = nfs.kpath()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    omega, infos, chunks = nfs.band_structure(g, med, ks, 10, precision="mixed", cg_tol=1e-10, eig_tol=1e-10)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"workload": "bands48: 48^3 chiral sphere r=0.25 (13, 1, 0.5), 40 k-points G-X-M-R-G, nev 10",
+            "seconds": dt, "eigenpairs_per_s": omega.size / dt, "kpoints_per_s": len(ks) / dt,
+            "chunks": chunks, "lanczos_steps_mean": float(sum(i.lanczos_steps for i in infos) / len(infos)),
+            "cg_iterations": int(sum(i.cg_iterations for i in infos)),
+            "band1_range": [float(omega[:, 0].min()), float(omega[:, 0].max())]}
+
+
+def mesh_leg(nfs, wl, torch):
+    """mesh: the mesh-convergence study of Section 5.1 (Fig. diff_mesh): the
+    three smallest omega of the chiral sphere (13, 1, 0.5) at k = (0.5, 0, 0)
+    on n^3 grids, n = 2^3 ... 2^7 (mixed precision)."""
+    out = []
+    for n in (8, 16, 32, 64, 128):
+        g = (n, n, n)
+        med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+        ctx = nfs.Context(g, (0.5, 0.0, 0.0), med, precision="mixed")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, _, info = ctx.eigs(3, vectors=False)
+        torch.cuda.synchronize()
+        out.append({"n": n, "omega": [float(x) for x in om], "seconds": time.perf_counter() - t0,
+                    "lanczos_steps": info.lanczos_steps})
+        ctx.close()
+    return {"workload": "mesh: chiral sphere r=0.25 (13, 1, 0.5), k=(0.5,0,0), nev 3, n^3 for n = 8..128",
+            "grids": out}
+
+
 def fields_leg(ctx, omega, Y, n, torch, hbm):
     """Algorithm 1's final step on the headline eigenpairs: the fields
     [E; H] = B^{-1} diag(P_r, Q_r) y of all NEV eigenvectors (nfs_eig_fields,
@@ -522,6 +564,8 @@ def run_ours(args):
     ctx.close()
     batch = None if (args.skip_batch or rank != 0) else batch_leg(nfs, wl, torch)
     grad = None if (args.skip_grad or rank != 0) else grad_leg(nfs, wl, torch, np)
+    bands = None if (args.skip_bands or rank != 0) else bands_leg(nfs, wl, torch)
+    mesh = None if (args.skip_mesh or rank != 0) else mesh_leg(nfs, wl, torch)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
@@ -558,6 +602,8 @@ def run_ours(args):
         "batch": batch,
         "gradient": grad,
         "fields": fields,
+        "bands": bands,
+        "mesh": mesh,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

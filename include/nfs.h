@@ -96,6 +96,14 @@ typedef struct {
                             * loss of A_r-orthogonality of a new vector to the
                             * older basis exceeds it, those components are
                             * removed; 0 = every step.  Default 1e-10            */
+  int deflation_checks;    /* Lanczos: after convergence, up to this many checks
+                            * for eigenvalues a single start vector misses (the
+                            * further copies of a degenerate one): lock the nev
+                            * Ritz vectors, restart from a random vector
+                            * A_r-orthogonal to them and converge the next
+                            * eigenvalue; a check that finds one among the nev
+                            * smallest takes it in and is followed by another.
+                            * 0 (default, the paper's procedure) = none; 0..16 */
   unsigned long long seed; /* starting-vector seed                                */
   void* stream;            /* cudaStream_t for every launch; NULL = default       */
 } nfs_options;
@@ -130,6 +138,7 @@ typedef struct {
   double seconds_orth;       /* orthogonality monitor and re-orthogonalisation     */
   double seconds_vectors;    /* forming the returned Ritz vectors                  */
   int reorthogonalisations;  /* steps that re-orthogonalised                       */
+  int deflation_checks;      /* deflation checks run (opt.deflation_checks)        */
 } nfs_eigs_info;
 
 /* Defaults: FP64, alpha = 2, beta = 3, cg_tol 1e-12, cg_maxit 2000,
@@ -284,6 +293,25 @@ int nfs_setup_batch(nfs_batch** out, int nprob, const nfs_problem* probs, const 
  * omega: HOST [nprob][nev]; info: HOST [nprob] or NULL.  Returns the worst
  * status (NFS_ENOCONV if any problem hit the restart cap). */
 int nfs_eigs_batch(nfs_batch* b, int nev, double* omega, nfs_eigs_info* info);
+
+/* Band structure: the nev smallest positive eigenvalues at each of nk Bloch
+ * vectors for one grid and one medium (the k sweeps of Section 5.3).  The
+ * k-points are solved in chunks, each chunk one batch (nfs_setup_batch,
+ * nfs_eigs_batch: one grid class, P problems in lock-step), as many per chunk
+ * as 80% of the free device memory holds with the full Lanczos basis of every
+ * problem (so no problem restarts), at most max_chunk if max_chunk > 0.
+ * Every k-point starts from its own random vector: starting Lanczos from the
+ * previous k-point's eigenvectors saves too few steps to be worth the risk of
+ * missing a band that enters from above.
+ *   grid, mat, opt: as for nfs_setup_batch (unit cube lattice).
+ *   k:      HOST [nk][3], Bloch vectors / 2 pi.
+ *   omega:  HOST [nk][nev], ascending per k-point.
+ *   info:   HOST [nk] or NULL.  chunks: HOST, the number of batches run, or NULL.
+ * Returns the worst status as nfs_eigs_batch; on an error in a chunk the rows
+ * of the earlier chunks are already written. */
+int nfs_band_structure(const int grid[3], const nfs_material* mat, int nk, const double* k,
+                       const nfs_options* opt, int nev, int max_chunk, double* omega,
+                       nfs_eigs_info* info, int* chunks);
 
 /* Number of grid classes the batch was split into. */
 int nfs_batch_num_classes(const nfs_batch* b);

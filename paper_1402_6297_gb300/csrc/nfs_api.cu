@@ -727,7 +727,6 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
   CK(cudaGetLastError());
   c->launches += 1;
 
-  const int keep = std::min(m - 1, std::max(nev + 1, nev + (m - nev) / 2));
   const int check_every = 5;
   std::vector<std::vector<double>> H(P, std::vector<double>((size_t)m * m, 0.0));
   std::vector<double> beta_last(P, 0.0);
@@ -750,6 +749,11 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       if (active[p]) return true;
     return false;
   };
+  // One Lanczos run over the active problems from basis position jstart
+  // until the nwant largest Ritz pairs of each have converged (thick restarts
+  // when the basis fills).
+  auto run = [&](int nwant) -> int {
+  const int keep = std::min(m - 1, std::max(nwant + 1, nwant + (m - nwant) / 2));
   TRY(put_flags(c, s, 0, active));
   while (any_active()) {
     for (int j = jstart; j < m && any_active(); ++j) {
@@ -830,7 +834,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       local_lo = j;
       // Ritz values of the leading (j+1) x (j+1) block; residual |beta z_last|
       const int k = j + 1;
-      if (k >= nev + 1 && ((k - jstart) % check_every == 0 || j == m - 1)) {
+      if (k >= nwant + 1 && ((k - jstart) % check_every == 0 || j == m - 1)) {
         bool changed = false;
         for (int p = 0; p < P; ++p) {
           if (!active[p]) continue;
@@ -840,12 +844,12 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
           c->sec_ritz += now_s() - th0;
           if (!ok) return NFS_EBREAKDOWN;
           int nc = 0;
-          for (int i = 0; i < nev; ++i) {
+          for (int i = 0; i < nwant; ++i) {
             const int cc = k - 1 - i;  // largest theta first
             if (std::fabs(beta_last[p] * zl[cc]) <= c->opt.eig_tol * std::fabs(theta[cc])) ++nc;
           }
-          nconv[p] = nc;
-          if (nc == nev) {
+          nconv[p] = std::min(nc, nev);
+          if (nc == nwant) {
             jm[p] = k;
             active[p] = 0;
             changed = true;
@@ -893,10 +897,89 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
     local_lo = 0;
     ++restarts;
   }
+  return NFS_OK;
+  };
+  TRY(run(nev));
+
+  // Deflation checks.  A single start vector has one component in each
+  // eigenspace, so the Krylov space holds one vector of a degenerate
+  // eigenvalue; its other copies enter only through rounding, possibly after
+  // the wanted pairs have converged.  Each check locks the nev converged Ritz
+  // vectors (basis positions 0..nev-1, decoupled: H = diag(theta)), restarts
+  // from a random vector A_r-orthogonal to them and runs until the next
+  // eigenvalue, the largest of the operator on their A_r-orthogonal
+  // complement, has converged too.  If it belongs among the nev largest (a
+  // missed copy), another check follows.
+  std::vector<int> one(P, 0), verified(P, 0), dchecks(P, 0);
+  for (int round = 0; round < c->opt.deflation_checks; ++round) {
+    std::vector<int> part(P, 0);
+    bool anyp = false;
+    for (int p = 0; p < P; ++p) {
+      part[p] = status[p] == NFS_OK && !verified[p];
+      anyp = anyp || part[p];
+    }
+    if (!anyp) break;
+    for (int p = 0; p < P; ++p) {
+      if (!part[p]) continue;
+      const int k = jm[p];
+      if (!nfs::host::sym_eig(k, leading(p, k), theta, Z)) return NFS_EBREAKDOWN;
+      std::vector<double> Ycm((size_t)P * k * nev, 0.0);
+      for (int i = 0; i < nev; ++i)
+        for (int r = 0; r < k; ++r) Ycm[(size_t)p * k * nev + (size_t)i * k + r] = Z[(size_t)r * k + (k - 1 - i)];
+      std::fill(one.begin(), one.end(), 0);
+      one[p] = 1;
+      TRY(put_flags(c, s, P, one));
+      TRY(rotate(c, c->V, k, Ycm, nev, c->d_flags + P));
+      TRY(rotate(c, c->MV, k, Ycm, nev, c->d_flags + P));
+      std::fill(H[p].begin(), H[p].end(), 0.0);
+      for (int i = 0; i < nev; ++i) H[p][(size_t)i * m + i] = theta[k - 1 - i];
+      beta_last[p] = 0.0;
+      ++dchecks[p];
+    }
+    active = part;
+    TRY(put_flags(c, s, 0, active));
+    TRY(refresh_shadows(c, 0, nev));
+    // the new start vector, A_r-orthogonalised twice against the locked ones
+    nfs::k_random_fill<<<nb, 256, 0, s>>>(c->V + (long long)nev * N, N, vstride, P,
+                                          c->opt.seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(round + 1));
+    CK(cudaGetLastError());
+    c->launches += 1;
+    for (int p = 0; p < P; ++p)
+      CK(cudaMemcpyAsync(w + p * N, col(c->V, p, nev), N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    TRY(matvec<double>(c, s, w, Mw));
+    for (int pass = 0; pass < 2; ++pass) {
+      TRY(multi_dot(c, c->MV, 0, nev, w, coef, d_active));
+      TRY(multi_axpy(c, w, Mw, 0, nev, coef, d_active));
+    }
+    TRY(dots_re(c, s, w, Mw, bb));
+    for (int p = 0; p < P; ++p) {
+      if (active[p] && !(bb[p] > 0)) return NFS_EBREAKDOWN;
+      sc[p] = active[p] ? 1.0 / std::sqrt(bb[p]) : 0.0;
+    }
+    TRY(put_small(c, s, P, sc));
+    nfs::k_store_basis_vector<<<nb, 256, 0, s>>>(w, Mw, c->d_small + P, c->V, c->MV, c->V32, c->MV32, c->MV32lo,
+                                                 vstride, nev, N, P, d_active);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    jstart = nev;
+    local_lo = 0;
+    TRY(run(nev + 1));
+    // a locked set is confirmed when the new block adds nothing to the nev
+    // largest Ritz pairs (its share of their invariant subspace is ~0)
+    for (int p = 0; p < P; ++p) {
+      if (!part[p] || status[p] != NFS_OK) continue;
+      const int k = jm[p];
+      if (!nfs::host::sym_eig(k, leading(p, k), theta, Z)) return NFS_EBREAKDOWN;
+      double mass = 0.0;
+      for (int i = 0; i < nev; ++i)
+        for (int r = nev; r < k; ++r) mass += Z[(size_t)r * k + (k - 1 - i)] * Z[(size_t)r * k + (k - 1 - i)];
+      verified[p] = mass < 0.5;
+    }
+  }
+
   // results from each problem's leading jm x jm block: omega ascending = theta descending
   const double tv0 = now_s();
   int worst = NFS_OK;
-  std::vector<int> one(P, 0);
   for (int p = 0; p < P; ++p) {
     const int k = jm[p];
     if (!nfs::host::sym_eig(k, leading(p, k), theta, Z)) return NFS_EBREAKDOWN;
@@ -937,6 +1020,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       in.seconds_orth = c->sec_orth - orth_0;
       in.seconds_vectors = now_s() - tv0;
       in.reorthogonalisations = reorths[p];
+      in.deflation_checks = dchecks[p];
     }
     if (status[p] != NFS_OK) worst = status[p];
   }
@@ -983,6 +1067,7 @@ int check_options(const nfs_options& o) {
   if (o.precision != NFS_PREC_FP64 && o.precision != NFS_PREC_MIXED) return NFS_EINVAL;
   if (!(o.cg_tol > 0) || o.cg_maxit <= 0 || !(o.eig_tol > 0) || o.max_restarts < 0) return NFS_EINVAL;
   if (!(o.orth_tol >= 0) || !(o.orth_tol < 1)) return NFS_EINVAL;
+  if (o.deflation_checks < 0 || o.deflation_checks > 16) return NFS_EINVAL;
   if (o.precision == NFS_PREC_MIXED && (!(o.inner_tol > 0) || o.inner_tol >= 1 || o.max_refine <= 0))
     return NFS_EINVAL;
   if (!(o.alpha != 0.0) || !(o.beta != 0.0)) return NFS_EBASIS;
@@ -1283,6 +1368,7 @@ extern "C" void nfs_default_options(nfs_options* o) {
   o->ncv = 0;
   o->max_restarts = 200;
   o->orth_tol = 1e-10;
+  o->deflation_checks = 0;
   o->seed = 1;
   o->stream = nullptr;
 }
@@ -1606,6 +1692,49 @@ extern "C" int nfs_eigs_batch(nfs_batch* b, int nev, double* omega, nfs_eigs_inf
     std::copy(om[ci].begin() + (size_t)q * nev, om[ci].begin() + (size_t)(q + 1) * nev, omega + (size_t)pi * nev);
     if (info) info[pi] = inf[ci][q];
   }
+  return worst;
+}
+
+extern "C" int nfs_band_structure(const int grid[3], const nfs_material* mat, int nk, const double* k,
+                                  const nfs_options* opt, int nev, int max_chunk, double* omega,
+                                  nfs_eigs_info* info, int* chunks) {
+  if (!grid || !mat || nk <= 0 || !k || nev <= 0 || !omega) return NFS_EINVAL;
+  const nfs_options o = resolved_options(opt);
+  TRY(check_options(o));
+  for (int l = 0; l < 3; ++l)
+    if (grid[l] <= 0) return NFS_EINVAL;
+  const double n = (double)grid[0] * grid[1] * grid[2];
+  // device bytes one k-point needs: its Lanczos basis at the full size (the
+  // same basis size nfs_eigs_batch would choose with room to spare: no
+  // restarts) and the fixed workspaces of a context (material copies, basis
+  // tables, fields, six complex128 and four complex64 vectors), rounded up
+  const int m = o.ncv > 0 ? o.ncv : wanted_ncv(nev);
+  const double per_k = (double)(m + 1) * 4.0 * n * (16 + 16 + 8 + 8 + 8) + 1024.0 * n;
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  int chunk = (int)std::min<double>(nk, std::max(1.0, std::floor(0.8 * (double)fr / per_k)));
+  if (max_chunk > 0) chunk = std::min(chunk, max_chunk);
+  int nchunks = 0, worst = NFS_OK;
+  std::vector<nfs_problem> probs;
+  for (int k0 = 0; k0 < nk; k0 += chunk) {
+    const int P = std::min(chunk, nk - k0);
+    probs.assign(P, nfs_problem{});
+    for (int q = 0; q < P; ++q) {
+      for (int l = 0; l < 3; ++l) {
+        probs[q].grid[l] = grid[l];
+        probs[q].k[l] = k[3 * (size_t)(k0 + q) + l];
+      }
+      probs[q].mat = *mat;
+    }
+    nfs_batch* b = nullptr;
+    TRY(nfs_setup_batch(&b, P, probs.data(), &o));
+    const int rc = nfs_eigs_batch(b, nev, omega + (size_t)k0 * nev, info ? info + k0 : nullptr);
+    nfs_destroy_batch(b);
+    ++nchunks;
+    if (rc != NFS_OK && rc != NFS_ENOCONV) return rc;
+    if (rc == NFS_ENOCONV) worst = rc;
+  }
+  if (chunks) *chunks = nchunks;
   return worst;
 }
 

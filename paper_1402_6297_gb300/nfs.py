@@ -72,6 +72,7 @@ class Options(ctypes.Structure):
         ("ncv", ctypes.c_int),
         ("max_restarts", ctypes.c_int),
         ("orth_tol", ctypes.c_double),
+        ("deflation_checks", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
         ("stream", ctypes.c_void_p),
     ]
@@ -116,6 +117,7 @@ class EigsInfo(ctypes.Structure):
         ("seconds_orth", ctypes.c_double),
         ("seconds_vectors", ctypes.c_double),
         ("reorthogonalisations", ctypes.c_int),
+        ("deflation_checks", ctypes.c_int),
     ]
 
 
@@ -176,6 +178,11 @@ def lib():
     L.nfs_setup_batch.restype = ip
     L.nfs_eigs_batch.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(EigsInfo)]
     L.nfs_eigs_batch.restype = ip
+    L.nfs_band_structure.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Material), ip,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Options), ip, ip,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(EigsInfo),
+                                     ctypes.POINTER(ctypes.c_int)]
+    L.nfs_band_structure.restype = ip
     L.nfs_batch_num_classes.argtypes = [vp]
     L.nfs_batch_num_classes.restype = ip
     L.nfs_destroy_batch.argtypes = [vp]
@@ -453,6 +460,61 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# High-symmetry points of the simple cubic Brillouin zone, Bloch vector / 2 pi
+# on the unit cube lattice.
+SC_POINTS = {"G": (0.0, 0.0, 0.0), "X": (0.5, 0.0, 0.0), "M": (0.5, 0.5, 0.0), "R": (0.5, 0.5, 0.5)}
+
+
+def kpath(corners=("G", "X", "M", "R", "G"), per_segment=10):
+    """Bloch vectors along the polyline through ``corners`` (names of
+    SC_POINTS or triples): ``per_segment`` uniformly spaced samples per
+    segment at the midpoints of its equal subintervals, which never land on a
+    corner, so Gamma (where Lambda_q is singular) is never sampled.  Returns
+    (k (m, 3), arc length at each k (m,))."""
+    pts = [np.asarray(SC_POINTS[c] if isinstance(c, str) else c, dtype=np.float64) for c in corners]
+    ks, arc, s0 = [], [], 0.0
+    for a, b in zip(pts[:-1], pts[1:]):
+        seg = float(np.linalg.norm(b - a))
+        for i in range(per_segment):
+            t = (i + 0.5) / per_segment
+            ks.append(a + t * (b - a))
+            arc.append(s0 + t * seg)
+        s0 += seg
+    return np.array(ks), np.array(arc)
+
+
+def band_structure(grid, medium, kpoints, nev, precision="mixed", max_chunk=0, stream=None, deflation_checks=2,
+                   **opts):
+    """The nev smallest positive omega at every Bloch vector of ``kpoints``
+    (m, 3) for one grid and medium (nfs_band_structure: chunks of k-points
+    solved as batches sized to the device memory).  Paths through
+    high-symmetry points meet degenerate eigenvalues, so by default every
+    solve runs two deflation checks (nfs_options.deflation_checks).  Returns
+    (omega (m, nev), list of EigsInfo, number of chunks)."""
+    opts["deflation_checks"] = deflation_checks
+    L = lib()
+    if float(getattr(medium, "a", 1.0)) != 1.0:
+        raise ValueError("band_structure uses the unit cube lattice")
+    k = np.ascontiguousarray(np.asarray(kpoints, dtype=np.float64).reshape(-1, 3))
+    nk = int(k.shape[0])
+    m, keep = _material(medium)
+    o = default_options()
+    o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+    for key, val in opts.items():
+        setattr(o, key, val)
+    o.stream = stream if stream is not None else _current_stream()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    omega = np.zeros((nk, nev), dtype=np.float64)
+    infos = (EigsInfo * nk)()
+    chunks = ctypes.c_int(0)
+    code = L.nfs_band_structure(g, ctypes.byref(m), nk, _dptr(k), ctypes.byref(o), int(nev), int(max_chunk),
+                                _dptr(omega), infos, ctypes.byref(chunks))
+    del keep
+    if code != NFS_OK:
+        raise NFSError(code, "nfs_band_structure")
+    return omega, [infos[i] for i in range(nk)], int(chunks.value)
 
 
 def matvec_noalloc(grid, kdota, kind, axes, eps, gamma, u, out, alpha=2.0, beta=3.0, stream=None):

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import workloads as wl  # noqa: E402
-from oracle import gep  # noqa: E402
+from oracle import gep, nfgep  # noqa: E402
 
 
 def write(name, header, values):
@@ -48,6 +48,33 @@ workload pseudo8: grid 8x8x8, 4 z-cylinders radius 0.1 (seed 0), eps 13 inside, 
 gamma = 0.4 everywhere, mu = 1, k.a = (0.1, 0.2, 0.3)
 oracle tier O1: dense Hermitian-definite pencil (oracle.gep.dense_eigs), FP64
 """, w[idx])
+
+    # mesh: the third validation of Section 5.1 (Fig. diff_mesh) -- the three
+    # smallest eigenvalues of the chiral sphere (13, 1, 0.5) at k = (0.5, 0, 0)
+    # on n^3 grids; tier O1 at 8^3, tier O2 (sparse shift-invert about
+    # sigma = 1.8, above half of every wanted omega) at 16^3, tier O3 (FFT
+    # NFGEP, ARPACK with CG) at 24^3 and 32^3.
+    rows = []
+    for n in (8, 16, 24, 32):
+        g = (n, n, n)
+        med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+        if n == 8:
+            w, _, idx = gep.dense_eigs(g, (0.5, 0.0, 0.0), med, 3)
+            om = w[idx[:3]]
+        elif n == 16:
+            om, _ = gep.sparse_eigs(g, (0.5, 0.0, 0.0), med, 3, sigma=1.8, tol=1e-12)
+        else:
+            om, _ = nfgep.NFGEP(g, (0.5, 0.0, 0.0), med).eigs(3, tol=1e-12, cg_tol=1e-13)
+        rows.append([n] + [float(x) for x in om])
+    with open(os.path.join(HERE, "mesh_sphere_omega.txt"), "w") as f:
+        f.write("""# 3 smallest positive eigenvalues omega of the discrete GEP (Sec. 3, eq. (discrete_GEP_EH))
+# on n x n x n grids (Sec. 5.1, third validation, Fig. diff_mesh): chiral sphere radius 0.25
+# centred in the unit cell, (eps_i, eps_o, gamma) = (13, 1, 0.5), mu = 1, k = (0.5, 0, 0)
+# oracle tier O1 (dense pencil) at n = 8, O2 (sparse shift-invert, sigma 1.8) at 16, O3 (FFT NFGEP) at 24, 32; FP64
+# columns: n, omega_1, omega_2, omega_3
+""")
+        for r in rows:
+            f.write(f"{r[0]:d} {r[1]:.17e} {r[2]:.17e} {r[3]:.17e}\n")
 
 
 if __name__ == "__main__":

@@ -177,3 +177,19 @@ def test_batch_validation_errors_without_gpu(nfs):
     assert L.nfs_eigs_batch(None, 3, None, None) == nfs.NFS_EINVAL
     assert L.nfs_batch_num_classes(None) == 0
     L.nfs_destroy_batch(None)
+
+
+def test_kpath_samples_segment_midpoints():
+    """The band path of Section 5.3 (G-X-M-R-G, ten samples per segment):
+    midpoints of equal subintervals, never a corner (Gamma is singular)."""
+    from paper_1402_6297_gb300 import nfs
+    ks, arc = nfs.kpath()
+    assert ks.shape == (40, 3)
+    assert np.all(np.diff(arc) > 0)
+    assert np.allclose(ks[0], (0.025, 0.0, 0.0)) and np.allclose(ks[9], (0.475, 0.0, 0.0))
+    assert np.allclose(ks[10], (0.5, 0.025, 0.0))
+    assert np.allclose(ks[-1], (0.025, 0.025, 0.025))
+    corners = np.array(list(nfs.SC_POINTS.values()))
+    assert np.min(np.linalg.norm(ks[:, None, :] - corners[None], axis=2)) > 0.02
+    ks2, _ = nfs.kpath(("X", (0.5, 0.5, 0.5)), per_segment=4)
+    assert np.allclose(ks2[:, 0], 0.5) and np.allclose(ks2[:, 1], ks2[:, 2])

@@ -1,0 +1,63 @@
+"""The band-structure driver (nfs_band_structure): chunked batches of
+k-points equal one-at-a-time solves, the oracle's eigenvalues, and the
+closed-form dispersion of a homogeneous medium (Section 5.1's second
+validation, the discrete plane waves written out)."""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import gep
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def test_chunks_equal_single_solves(lib):
+    g = (12, 12, 12)
+    med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+    ks, _ = lib.kpath(per_segment=2)  # 8 k-points
+    omega, infos, chunks = lib.band_structure(g, med, ks, 6, precision="mixed", max_chunk=3,
+                                              cg_tol=1e-10, eig_tol=1e-10)
+    assert chunks == 3  # 3 + 3 + 2
+    assert omega.shape == (8, 6)
+    assert np.all(np.diff(omega, axis=1) >= 0)
+    for i in (0, 4, 7):
+        ctx = lib.Context(g, tuple(ks[i]), med, precision="mixed", cg_tol=1e-10, eig_tol=1e-10)
+        om, _, _ = ctx.eigs(6, vectors=False)
+        ctx.close()
+        assert np.abs(omega[i] - om).max() < 1e-8 * om.max()
+    assert all(inf.nconv >= 6 for inf in infos)
+
+
+def test_matches_oracle(lib):
+    g = (8, 8, 8)
+    med = wl.pseudochiral_cylinders(g, 2, 0.2, 13.0, 1.0, 0.5, (0, 2), 4)
+    ks = np.array([[0.1, 0.2, 0.3], [0.45, 0.05, 0.0], [0.25, 0.25, 0.25]])
+    omega, _, chunks = lib.band_structure(g, med, ks, 8, precision="fp64")
+    assert chunks == 1
+    for i in range(3):
+        w, _, idx = gep.dense_eigs(g, tuple(ks[i]), med)
+        ref = w[idx[:8]]
+        assert np.abs(omega[i] - ref).max() < 1e-10 * ref.max()
+
+
+def test_homogeneous_dispersion(lib):
+    """eps = 4, gamma = 0: omega = sqrt(Lambda_q) / 2, each twice."""
+    g = (16, 16, 16)
+    n1, n2, n3 = g
+    med = wl.homogeneous(g, eps=4.0)
+    ks, _ = lib.kpath(("X", "M", "R"), per_segment=3)
+    # Cubic symmetry and the two polarisations make clusters of up to eight
+    # equal eigenvalues on these lines: a single start vector holds one copy
+    # of each, so the solve needs up to seven deflation checks.  The clusters'
+    # eigenvalue errors are first order in the Ritz residual (eig_tol 1e-10).
+    omega, infos, _ = lib.band_structure(g, med, ks, 8, precision="fp64", deflation_checks=8)
+    i3, i2, i1 = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    for k, om in zip(ks, omega):
+        lq = (4 * np.sin(np.pi * (i1 + k[0]) / n1) ** 2 * n1 ** 2
+              + 4 * np.sin(np.pi * (i2 + k[1]) / n2) ** 2 * n2 ** 2
+              + 4 * np.sin(np.pi * (i3 + k[2]) / n3) ** 2 * n3 ** 2).ravel()
+        ref = np.sort(np.concatenate([np.sqrt(lq), np.sqrt(lq)]) / 2.0)[:8]
+        assert np.abs(om - ref).max() < 1e-9 * ref.max()
+    assert max(i.deflation_checks for i in infos) >= 2

@@ -137,3 +137,25 @@ def test_eig_gradient_pseudochiral(nfs):
     assert np.abs(d_eps.cpu().numpy() - re).max() / np.abs(re).max() < 1e-6
     assert np.abs(d_gam.cpu().numpy() - rg).max() / np.abs(rg).max() < 1e-6
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_deflation_checks_find_degenerate_copies(nfs, precision):
+    """At k.a = (0.45, 0.05, 0) the z-invariant cylinders keep the mirror
+    symmetry z -> -z and this medium has a double eigenvalue at positions 7
+    and 8 (oracle).  With deflation checks the solver returns both copies;
+    every check it ran is reported."""
+    g = (8, 8, 8)
+    k = (0.45, 0.05, 0.0)
+    med = wl.pseudochiral_cylinders(g, 2, 0.2, 13.0, 1.0, 0.5, (0, 2), 4)
+    w, _, idx = gep.dense_eigs(g, k, med)
+    ref = w[idx[:8]]
+    assert abs(ref[7] - ref[6]) < 1e-10 * ref[7]  # the degenerate pair
+    ctx = nfs.Context(g, k, med, precision=precision, deflation_checks=3)
+    omega, Y, info = ctx.eigs(8)
+    assert np.abs(omega - ref).max() < 1e-9 * ref.max()
+    assert 1 <= info.deflation_checks <= 3
+    # the returned vectors are A_r-orthonormal eigenvectors, the pair included
+    res = nfs.residuals(ctx, omega, Y)
+    assert max(res) < 1e-8
+    ctx.close()
