@@ -27,6 +27,11 @@ media"):
   x = [E; H] = B^{-1} diag(P_r, Q_r) y of Algorithm 1's final step; with
   :func:`oracle.gep.gep_residual`, the relative residual of (omega, x) in the
   GEP itself.
+* :mod:`oracle.nfsep` -- Section 4 (thm:nfep) and Algorithm 1's second branch:
+  the null space free standard eigenproblem (eq. NFSEP_org) for any
+  nonsingular B (media outside the Assumption: lossy, non-reciprocal,
+  strongly coupled bi-isotropic), shift-and-invert Arnoldi with GMRES, and the
+  field recovery of that branch.
 
 Readings of the paper that the oracle fixes (the paper is silent or misprints):
 

@@ -14,7 +14,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from workloads.media import CHIRAL, PSEUDOCHIRAL, Medium
+from workloads.media import BIISOTROPIC, CHIRAL, PSEUDOCHIRAL, Medium
 
 
 def tensors(medium: Medium):
@@ -33,6 +33,15 @@ def tensors(medium: Medium):
         for c in range(3):
             xi[c, c] = 1j * medium.gamma[c]
             zeta[c, c] = -1j * medium.gamma[c]
+    elif medium.kind == BIISOTROPIC:
+        # bi-isotropic constitutive relations written in the GEP's blocks:
+        # xi_d = (chi + i gamma) I~, zeta_d = (chi - i gamma) I~ per component;
+        # chi = 0 is the chiral medium above.  With complex parameters (loss)
+        # or chi^2 + gamma^2 >= eps mu the Assumption fails.
+        chi = np.zeros_like(medium.gamma) if medium.chi is None else medium.chi
+        for c in range(3):
+            xi[c, c] = chi[c] + 1j * medium.gamma[c]
+            zeta[c, c] = chi[c] - 1j * medium.gamma[c]
     elif medium.kind == PSEUDOCHIRAL:
         # eq. (pseudo_chiral_para_mtx): i gamma I~_n in the two off-diagonal
         # blocks coupling the chosen axis pair (x-z in the paper).
@@ -89,8 +98,11 @@ def assumption_holds(medium: Medium):
         return False
     phi = eps - tmul(tmul(xi, batched_inv(mu)), zeta)
     for t in (mu, phi):
+        # "mu_d > 0, Phi > 0" are Hermitian positive definite (eq. (assump))
         m = np.moveaxis(t.reshape(3, 3, -1), -1, 0)
-        h = 0.5 * (m + np.conj(np.swapaxes(m, 1, 2)))
-        if np.min(np.linalg.eigvalsh(h)) <= 0:
+        mh = np.conj(np.swapaxes(m, 1, 2))
+        if not np.allclose(m, mh):
+            return False
+        if np.min(np.linalg.eigvalsh(0.5 * (m + mh))) <= 0:
             return False
     return True

@@ -218,6 +218,8 @@ def _dptr(a: np.ndarray):
 
 def _material(medium):
     """nfs_material over host copies of the medium (returned to keep alive)."""
+    if medium.kind not in ("chiral", "pseudochiral"):
+        raise ValueError(f"the CUDA library solves chiral and pseudochiral media, not {medium.kind!r}")
     eps = np.ascontiguousarray(medium.eps, dtype=np.float64)
     gam = np.ascontiguousarray(medium.gamma, dtype=np.float64)
     mu = None if medium.mu is None else np.ascontiguousarray(medium.mu, dtype=np.float64)

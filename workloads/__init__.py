@@ -9,6 +9,7 @@ here, each with its own implementation of the method.
 
 from .media import (  # noqa: F401
     Medium,
+    biisotropic_sphere,
     bz_path_midpoints,
     chiral_sphere,
     homogeneous,

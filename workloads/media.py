@@ -20,6 +20,9 @@ A :class:`Medium` is a plain record of per-component real arrays:
 * chiral:        eps[3][n3][n2][n1] > 0, gamma[3][n3][n2][n1], mu = None (1)
 * pseudochiral:  eps[3][...], gamma[n3][n2][n1] (one coupling per voxel),
                  coupled axis pair ``axes`` = (a, b), mu = None (1)
+* biisotropic:   eps[3][...] and mu[3][...] (complex allowed: loss),
+                 gamma[3][...] and chi[3][...] (complex allowed): the
+                 chirality and Tellegen parameters of each component
 
 Turning these into the magnetoelectric tensors xi, zeta is the method's job
 and is done separately by each consumer.
@@ -35,6 +38,7 @@ import numpy as np
 
 CHIRAL = "chiral"
 PSEUDOCHIRAL = "pseudochiral"
+BIISOTROPIC = "biisotropic"
 
 
 @dataclasses.dataclass
@@ -46,6 +50,7 @@ class Medium:
     mu: Optional[np.ndarray] = None  # (3, n3, n2, n1) or None meaning mu = 1
     axes: Tuple[int, int] = (0, 1)   # pseudochiral coupled pair
     a: float = 1.0
+    chi: Optional[np.ndarray] = None  # biisotropic Tellegen parameter (3, n3, n2, n1)
 
     @property
     def n(self) -> int:
@@ -100,6 +105,25 @@ def chiral_sphere(grid, radius=0.25, eps_in=13.0, eps_out=1.0, gamma=0.5,
         eps[c] = np.where(ind, eps_in, eps_out)
         gam[c] = np.where(ind, gamma, 0.0)
     return Medium(tuple(grid), CHIRAL, eps, gam, None, (0, 1), a)
+
+
+def biisotropic_sphere(grid, radius=0.25, eps_in=13.0, eps_out=1.0, gamma=0.5, chi=0.0, mu_in=1.0,
+                       center=(0.5, 0.5, 0.5), a=1.0) -> Medium:
+    """Bi-isotropic sphere: eps_in, mu_in, chirality gamma and Tellegen
+    parameter chi inside (complex values allowed); eps_out, 1, 0, 0 outside."""
+    n1, n2, n3 = grid
+    shape = (3, n3, n2, n1)
+    eps = np.empty(shape, np.complex128)
+    mu = np.empty(shape, np.complex128)
+    gam = np.empty(shape, np.complex128)
+    ch = np.empty(shape, np.complex128)
+    for c in range(3):
+        ind = sphere_indicator(grid, center, radius, c, a)
+        eps[c] = np.where(ind, eps_in, eps_out)
+        mu[c] = np.where(ind, mu_in, 1.0)
+        gam[c] = np.where(ind, gamma, 0.0)
+        ch[c] = np.where(ind, chi, 0.0)
+    return Medium(tuple(grid), BIISOTROPIC, eps, gam, mu, (0, 1), a, ch)
 
 
 def homogeneous(grid, eps=1.0, gamma=0.0, a=1.0) -> Medium:
