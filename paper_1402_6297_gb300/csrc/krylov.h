@@ -1,0 +1,70 @@
+// Host drivers of the non-Hermitian Krylov methods for the null space free
+// standard problem M y = omega y (eq. NFSEP_org) outside the Assumption:
+// restarted GMRES for the shifted systems (M - sigma I) z = b, and
+// Krylov-Schur Arnoldi on (M - sigma I)^{-1} for the eigenvalues nearest the
+// shift (shift-and-invert Arnoldi, Section 4).  The drivers own the small
+// projected matrices; every operation on the long vectors goes through a
+// KrylovOps object, so the same driver runs on device vectors (the library)
+// or on host vectors (the CPU tests).
+#pragma once
+#include <complex>
+#include <vector>
+
+namespace nfs {
+namespace host {
+
+using cplxd = std::complex<double>;
+
+// A basis V_0 .. V_{cap-1} of long vectors and one work vector w.  Every
+// call returns 0 (NFS_OK) or a negative library error code.
+struct KrylovOps {
+  virtual ~KrylovOps() = default;
+  virtual int apply(int j) = 0;                                   // w = Op V_j
+  virtual int dots(int m, std::vector<cplxd>& c) = 0;             // c_i = V_i^* w, i < m
+  virtual int axpy(int m, const std::vector<cplxd>& c) = 0;       // w -= sum_{i<m} c_i V_i
+  virtual int norm(double& nrm) = 0;                              // ||w||_2
+  virtual int store(int j, double scale) = 0;                     // V_j = scale w
+  // V_i <- sum_{r<m} V_r Q[r * k + i] for i < k (Q row-major m x k)
+  virtual int rotate(int m, const std::vector<cplxd>& Q, int k) = 0;
+  virtual int copy(int dst, int src) = 0;                         // V_dst = V_src
+  virtual int load(int j) = 0;                                    // w = V_j
+};
+
+// Operations GMRES needs beyond the basis: the right-hand side, the
+// iterate x and the residual.
+struct GmresOps : virtual KrylovOps {
+  virtual int residual() = 0;                                     // w = b - Op x
+  virtual int update(int m, const std::vector<cplxd>& y) = 0;     // x += sum_{i<m} y_i V_i
+};
+
+struct GmresResult {
+  int iterations = 0;   // operator applications
+  int restarts = 0;
+  double relres = 0.0;  // final ||b - Op x|| / ||b||
+  int status = 0;       // 0 or NFS_ENOCONV (-6)
+};
+
+// Restarted GMRES(m) from the iterate the ops hold, modified Gram-Schmidt
+// with one re-orthogonalisation pass, Givens rotations on the Hessenberg
+// matrix.  Stops at ||r|| <= tol ||b|| (bnorm = ||b||) or after maxit
+// operator applications.
+int gmres(GmresOps& ops, int m, double tol, double bnorm, int maxit, GmresResult& out);
+
+struct ArnoldiResult {
+  std::vector<cplxd> theta;  // the nev eigenvalues of Op of largest modulus
+  int steps = 0;             // operator applications
+  int restarts = 0;
+  int nconv = 0;
+  double max_residual = 0.0; // max |h_{m+1,m} s_m| / |theta| over the nev
+  int status = 0;            // 0 or NFS_ENOCONV (-6)
+};
+
+// Krylov-Schur Arnoldi for the nev eigenvalues of Op of largest modulus
+// (Op = (M - sigma I)^{-1}: the eigenvalues of M nearest sigma).  V_0 must
+// hold a start vector on entry.  Basis size m (nev + 2 <= m < cap); on
+// return V_0 .. V_{nev-1} hold unit eigenvectors of the nev values, in the
+// order of res.theta (largest modulus first).
+int krylov_schur(KrylovOps& ops, int nev, int m, double tol, int max_restarts, ArnoldiResult& res);
+
+}  // namespace host
+}  // namespace nfs
