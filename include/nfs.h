@@ -235,6 +235,66 @@ int nfs_eig_fields(nfs_ctx* ctx, int m, const void* Y, void* X);
  * Synchronises opt.stream.  Single-problem contexts only. */
 int nfs_gep_residual(nfs_ctx* ctx, int m, const double* omega, const void* X, double* res);
 
+/* ---- media outside the Assumption: the NFSEP (Algorithm 1, 2nd branch) --
+ *
+ * For a nonsingular B that violates the Assumption (loss, non-reciprocal or
+ * strong magnetoelectric coupling) the HHPD-NFGEP does not apply; the GEP's
+ * nonzero eigenvalues are those of the null space free standard problem
+ * (thm:nfep, eq. NFSEP_org)
+ *   M y = omega y,  M = diag(S Q_r^*, S P_r^*) B^{-1} diag(P_r S, Q_r S),
+ *   S = Sigma_r^{1/2},
+ * which is not Hermitian; its eigenvalues are complex in general.  These
+ * calls work in complex128 throughout. */
+
+/* Bi-isotropic medium: per component and voxel, complex arrays [3][n3][n2][n1]
+ * stored as interleaved (re, im) doubles; xi = chi + i gamma and
+ * zeta = chi - i gamma (chi = 0 is the chiral medium of nfs_material). */
+typedef struct {
+  const double* eps;    /* permittivity                                        */
+  const double* mu;     /* permeability, or NULL meaning 1                     */
+  const double* gamma;  /* chirality parameter                                 */
+  const double* chi;    /* Tellegen parameter, or NULL meaning 0               */
+} nfs_biiso_material;
+
+/* Set up a context for a bi-isotropic medium (grid, lattice, k and opt as
+ * for nfs_setup; the material is copied).  Stores B^{-1} per voxel as one
+ * 2 x 2 complex block per component; NFS_EINVAL if B is singular anywhere.
+ * Only the nfs_nfsep_* calls (and nfs_destroy) apply to such a context; the
+ * A_r calls return NFS_EUNSUPPORTED. */
+int nfs_setup_biiso(nfs_ctx** out, const int grid[3], const double* lattice, const double k[3],
+                    const nfs_biiso_material* mat, const nfs_options* opt);
+
+/* My = M y (eq. NFSEP_org).  y, My: DEVICE complex128, 4n each, in the
+ * layout of nfs_matvec's vectors, 16-byte aligned, distinct.  Stream-ordered
+ * on opt.stream. */
+int nfs_nfsep_matvec(nfs_ctx* ctx, const void* y, void* My);
+
+typedef struct {
+  int arnoldi_steps;          /* shift-inverted operator applications         */
+  int restarts;               /* Krylov-Schur restarts                         */
+  long long gmres_iterations; /* products inside the GMRES solves              */
+  int nconv;                  /* wanted Ritz pairs that met eig_tol            */
+  double max_ritz_residual;   /* max over them of the relative Ritz residual   */
+  int status;                 /* NFS_OK or NFS_ENOCONV                          */
+  long long kernel_launches;
+} nfs_nfsep_info;
+
+/* The nev eigenvalues of M nearest the complex shift sigma = {re, im}:
+ * Krylov-Schur Arnoldi on (M - sigma I)^{-1} (shift-and-invert Arnoldi,
+ * Section 4), each inverse applied by restarted GMRES(100) to a relative
+ * residual of opt.cg_tol (at most opt.cg_maxit products); basis opt.ncv or
+ * max(2 nev + 2, 20); Ritz pairs accepted at opt.eig_tol.
+ *   omega: HOST, 2 nev doubles (re, im), nearest sigma first.
+ *   Y:     DEVICE complex128 [nev][4n] unit eigenvectors y of M, or NULL.
+ * Synchronises opt.stream; allocates the Arnoldi and GMRES bases on first
+ * use.  Returns NFS_ENOCONV (results written) if the restart cap is hit. */
+int nfs_nfsep_eigs(nfs_ctx* ctx, int nev, const double sigma[2], double* omega, void* Y, nfs_nfsep_info* info);
+
+/* Fields of NFSEP eigenvectors (Algorithm 1, second branch): y <- S y, then
+ * x = [E; H] = B^{-1} diag(P_r, Q_r) y, Bloch twist included.
+ *   Y: DEVICE complex128 [m][4n];  X: DEVICE complex128 [m][6][n3][n2][n1]. */
+int nfs_nfsep_fields(nfs_ctx* ctx, int m, const void* Y, void* X);
+
 /* ---- allocation-free product ------------------------------------------ */
 
 /* Largest voxel count n1*n2*n3 that nfs_matvec_noalloc accepts (32^3). */

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBNAME = "libnfs.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["nfs_api.cu", "matvec_f32.cu", "matvec_f64.cu", "matvec_df.cu", "noalloc.cu", "host_eig.cpp", "host_zeig.cpp", "krylov.cpp"]
+SOURCES = ["nfs_api.cu", "matvec_f32.cu", "matvec_f64.cu", "matvec_df.cu", "noalloc.cu", "host_eig.cpp", "host_zeig.cpp", "krylov.cpp", "nfsep.cu"]
 
 
 def nvcc_path():

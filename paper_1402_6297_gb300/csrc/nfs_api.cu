@@ -29,7 +29,9 @@
 #include "blas_kernels.cuh"
 #include "dfloat.cuh"
 #include "host_eig.h"
+#include "krylov.h"
 #include "matvec.h"
+#include "nfsep.h"
 
 using nfs::CGState;
 using nfs::kRedBlocks;
@@ -67,6 +69,15 @@ struct nfs_ctx {
   // D_l[j] = exp(i 2 pi k.a_l j / n_l), l = 1, 2, 3; and k.a_l itself
   double2* bloch64 = nullptr;
   std::vector<double> kd;
+  // media outside the Assumption (nfs_setup_biiso): B^{-1} per voxel and
+  // component as 2 x 2 blocks [4 * 3][n]; the Arnoldi and GMRES bases and the
+  // device copy of rotation coefficients of the NFSEP eigensolve
+  double2* binv64 = nullptr;
+  double2* zv = nullptr;
+  double2* gv = nullptr;
+  double* zY = nullptr;
+  int zv_cap = 0, gv_cap = 0;
+  size_t zY_len = 0;
   // double-single copies of the tables, material and basis (mixed contexts:
   // the refinement residual products)
   nfs::dfc* lamdf = nullptr;
@@ -1043,7 +1054,7 @@ void free_ctx(nfs_ctx* c) {
                   c->mat64, c->mat32, c->basis64, c->bloch64, c->lamdf, c->twdf[0], c->twdf[1], c->twdf[2], c->matdf,
                   c->basisdf, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
                   c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
-                  c->MV32lo, c->dY};
+                  c->MV32lo, c->dY, c->binv64, c->zv, c->gv, c->zY};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -1425,6 +1436,7 @@ extern "C" int nfs_set_stream(nfs_ctx* c, void* stream) {
 
 extern "C" int nfs_matvec(nfs_ctx* c, int dtype, const void* u, void* Au) {
   if (!c || !u || !Au || u == Au) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;  // no A_r outside the Assumption
   if (((uintptr_t)u | (uintptr_t)Au) & 15) return NFS_EINVAL;  // 16-byte vector access
   if (dtype == NFS_C128) return matvec<double>(c, c->stream, (const double2*)u, (double2*)Au);
   if (dtype == NFS_C64) return matvec<float>(c, c->stream, (const float2*)u, (float2*)Au);
@@ -1437,6 +1449,7 @@ extern "C" int nfs_matvec(nfs_ctx* c, int dtype, const void* u, void* Au) {
 
 extern "C" int nfs_matvec_passes(nfs_ctx* c, int dtype, int mask, const void* u, void* Au) {
   if (!c || mask <= 0 || mask > 7) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;
   if ((mask & 1) && !u) return NFS_EINVAL;
   if ((mask & 4) && !Au) return NFS_EINVAL;
   if (((uintptr_t)u | (uintptr_t)Au) & 15) return NFS_EINVAL;
@@ -1453,6 +1466,7 @@ extern "C" int nfs_matvec_passes(nfs_ctx* c, int dtype, int mask, const void* u,
 
 extern "C" int nfs_apply_Br(nfs_ctx* c, const void* v, void* out) {
   if (!c || !v || !out || v == out) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;
   nfs::k_apply_Br<<<grid_blocks(c->n * c->P, 256), 256, 0, c->stream>>>((const double2*)v, (double2*)out, c->lam64,
                                                                           c->n1, c->n2, c->n3, c->P);
   CK(cudaGetLastError());
@@ -1461,6 +1475,7 @@ extern "C" int nfs_apply_Br(nfs_ctx* c, const void* v, void* out) {
 
 extern "C" int nfs_cg_solve(nfs_ctx* c, const void* b, void* x, nfs_solve_info* info) {
   if (!c || !b || !x || b == x) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;
   if (((uintptr_t)b | (uintptr_t)x) & 15) return NFS_EINVAL;
   TRY(join_caller(c));
   // the solve runs on the context's buffers (so that its CUDA graph is reused)
@@ -1483,6 +1498,7 @@ extern "C" int nfs_cg_solve(nfs_ctx* c, const void* b, void* x, nfs_solve_info* 
 
 extern "C" int nfs_eigs(nfs_ctx* c, int nev, double* omega, void* Y, nfs_eigs_info* info) {
   if (!c || !omega || nev <= 0 || nev >= c->N / 2) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;
   TRY(join_caller(c));
   return eigs_core(c, nev, omega, (double2*)Y, info);
 }
@@ -1490,7 +1506,7 @@ extern "C" int nfs_eigs(nfs_ctx* c, int nev, double* omega, void* Y, nfs_eigs_in
 extern "C" int nfs_eig_grad(nfs_ctx* c, int m, const double* weights, const void* Yv, double* d_eps,
                             double* d_gamma) {
   if (!c || m <= 0 || !weights || !Yv) return NFS_EINVAL;
-  if (c->has_mu || c->P != 1) return NFS_EUNSUPPORTED;
+  if (c->has_mu || c->P != 1 || c->binv64) return NFS_EUNSUPPORTED;
   TRY(join_caller(c));
   cudaStream_t s = c->work;
   const long long n = c->n, N = c->N;
@@ -1525,7 +1541,7 @@ extern "C" int nfs_eig_grad(nfs_ctx* c, int m, const double* weights, const void
 extern "C" int nfs_eig_fields(nfs_ctx* c, int m, const void* Yv, void* Xv) {
   if (!c || m <= 0 || !Yv || !Xv) return NFS_EINVAL;
   if ((((uintptr_t)Yv) | ((uintptr_t)Xv)) & 15) return NFS_EINVAL;
-  if (c->P != 1) return NFS_EUNSUPPORTED;
+  if (c->P != 1 || c->binv64) return NFS_EUNSUPPORTED;
   const long long n = c->n, N = c->N;
   const double2* Y = (const double2*)Yv;
   double2* X = (double2*)Xv;
@@ -1550,7 +1566,7 @@ extern "C" int nfs_eig_fields(nfs_ctx* c, int m, const void* Yv, void* Xv) {
 
 extern "C" int nfs_gep_residual(nfs_ctx* c, int m, const double* omega, const void* Xv, double* res) {
   if (!c || m <= 0 || !omega || !Xv || !res) return NFS_EINVAL;
-  if (c->P != 1) return NFS_EUNSUPPORTED;
+  if (c->P != 1 || c->binv64) return NFS_EUNSUPPORTED;
   for (int j = 0; j < m; ++j)
     if (!(std::isfinite(omega[j]) && omega[j] != 0.0)) return NFS_EINVAL;
   const long long n = c->n;
@@ -1581,6 +1597,301 @@ extern "C" int nfs_gep_residual(nfs_ctx* c, int m, const double* omega, const vo
       b2 += c->hscratch[2 * i + 1];
     }
     res[j] = std::sqrt(r2) / (std::fabs(omega[j]) * std::sqrt(b2));
+  }
+  return NFS_OK;
+}
+
+// --- media outside the Assumption: the NFSEP --------------------------------
+
+namespace {
+
+// M y (- sigma v) on the given stream: Sigma^{1/2}, pass 1, the B^{-1} z-pass,
+// pass 3, halves exchanged and Sigma^{1/2} (t64 and Ap64 are its temporaries)
+int nfsep_apply(nfs_ctx* c, cudaStream_t s, const double2* y, double2* out, const double2* v, double2 sigma) {
+  cudaError_t e = nfs::nfsep_prescale(y, c->t64, c->lam64, c->n1, c->n2, c->n3, s);
+  if (e != cudaSuccess) return cuda_fail(e, "nfsep prescale");
+  nfs::MatvecArgs<double> a = margs<double>(c, c->t64, c->Ap64, nullptr);
+  a.stream = s;
+  e = nfs::pass1_launch<double>(a);
+  if (e != cudaSuccess) return cuda_fail(e, "nfsep pass 1");
+  e = nfs::nfsep_pass2((double2*)c->fld, c->binv64, c->tw64[2], c->n1, c->n2, c->n3, s);
+  if (e != cudaSuccess) return cuda_fail(e, "nfsep pass 2");
+  e = nfs::matvec_launch_mask<double>(a, 4);
+  if (e != cudaSuccess) return cuda_fail(e, "nfsep pass 3");
+  e = nfs::nfsep_post(c->Ap64, out, c->lam64, c->n1, c->n2, c->n3, v, sigma, s);
+  if (e != cudaSuccess) return cuda_fail(e, "nfsep post");
+  c->launches += 5;
+  return NFS_OK;
+}
+
+using nfs::host::cplxd;
+
+// Long-vector operations of the Krylov drivers on device vectors (P = 1):
+// basis V (vector j at V + j N) and work vector w, on the context's stream.
+struct DevBasis : virtual nfs::host::KrylovOps {
+  nfs_ctx* c;
+  double2* V;
+  double2* w;
+  long long N;
+  cudaStream_t s;
+  DevBasis(nfs_ctx* ctx, double2* basis, double2* work) : c(ctx), V(basis), w(work), N(ctx->N), s(ctx->stream) {}
+  int put_coef(const std::vector<cplxd>& cf, double* dst) {
+    for (size_t i = 0; i < cf.size(); ++i) {
+      c->hscratch[2 * i] = cf[i].real();
+      c->hscratch[2 * i + 1] = cf[i].imag();
+    }
+    CK(cudaMemcpyAsync(dst, c->hscratch, cf.size() * 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+    return NFS_OK;
+  }
+  int dots(int m, std::vector<cplxd>& out) override {
+    double* part = c->dscratch;
+    double* fin = c->dscratch + (size_t)kRedBlocks * 2 * m;
+    nfs::k_multi_dot<kRedThreads><<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(V, 0, m, w, N, part, nullptr);
+    nfs::k_multi_dot_finish<<<dim3(m, 1), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, nullptr);
+    CK(cudaGetLastError());
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    out.resize(m);
+    for (int i = 0; i < m; ++i) out[i] = cplxd(c->hscratch[2 * i], c->hscratch[2 * i + 1]);
+    return NFS_OK;
+  }
+  int axpy(int m, const std::vector<cplxd>& cf) override {
+    double* dc = c->dscratch;
+    TRY(put_coef(cf, dc));
+    CK(nfs::zaxpy_basis(w, V, N, dc, m, 1.0, s));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(s));  // the pinned staging buffer is reused next
+    return NFS_OK;
+  }
+  int norm(double& nrm) override {
+    nfs::k_dot_re<double2><<<dim3(kRedBlocks, 1), kRedThreads, 0, s>>>(w, w, N, c->dscratch, kRedBlocks, nullptr, 0);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    CK(cudaMemcpyAsync(c->hscratch, c->dscratch, kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (int i = 0; i < kRedBlocks; ++i) t += c->hscratch[i];
+    nrm = std::sqrt(std::max(t, 0.0));
+    return NFS_OK;
+  }
+  int store(int j, double scale) override {
+    CK(nfs::zscale_copy(w, V + (long long)j * N, scale, N, s));
+    c->launches += 1;
+    return NFS_OK;
+  }
+  int rotate(int m, const std::vector<cplxd>& Q, int k) override {
+    const size_t need = (size_t)m * k * 2;
+    if (c->zY_len < need) {
+      if (c->zY) cudaFree(c->zY);
+      c->zY = nullptr;
+      TRY(dalloc(c, &c->zY, need));
+      c->zY_len = need;
+    }
+    std::vector<double> h(need);
+    for (size_t i = 0; i < Q.size(); ++i) {
+      h[2 * i] = Q[i].real();
+      h[2 * i + 1] = Q[i].imag();
+    }
+    CK(cudaMemcpyAsync(c->zY, h.data(), need * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(nfs::zrotate(V, m, c->zY, k, N, s));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(s));  // h is released next
+    return NFS_OK;
+  }
+  int copy(int dst, int src) override {
+    CK(cudaMemcpyAsync(V + (long long)dst * N, V + (long long)src * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    return NFS_OK;
+  }
+  int load(int j) override {
+    CK(cudaMemcpyAsync(w, V + (long long)j * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    return NFS_OK;
+  }
+};
+
+// GMRES on (M - sigma I) x = b
+struct DevGmres : DevBasis, nfs::host::GmresOps {
+  const double2* b = nullptr;
+  double2* x;
+  double2 sigma;
+  DevGmres(nfs_ctx* ctx, double2* basis, double2* work, double2* xv, double2 sg)
+      : DevBasis(ctx, basis, work), x(xv), sigma(sg) {}
+  int apply(int j) override { return nfsep_apply(c, s, V + (long long)j * N, w, V + (long long)j * N, sigma); }
+  int residual() override {
+    TRY(nfsep_apply(c, s, x, w, x, sigma));
+    nfs::k_sub<double2><<<grid_blocks(N, 256), 256, 0, s>>>(b, w, w, N);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    return NFS_OK;
+  }
+  int update(int m, const std::vector<cplxd>& y) override {
+    double* dc = c->dscratch;
+    TRY(put_coef(y, dc));
+    CK(nfs::zaxpy_basis(x, V, N, dc, m, -1.0, s));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(s));
+    return NFS_OK;
+  }
+};
+
+// Arnoldi on (M - sigma I)^{-1}: each application one GMRES solve
+struct DevShiftInvert : DevBasis {
+  DevGmres& g;
+  int gm;
+  double tol;
+  int maxit;
+  long long inner = 0;
+  DevShiftInvert(nfs_ctx* ctx, double2* basis, double2* work, DevGmres& gg, int m_inner, double t, int mi)
+      : DevBasis(ctx, basis, work), g(gg), gm(m_inner), tol(t), maxit(mi) {}
+  int apply(int j) override {
+    g.b = V + (long long)j * N;
+    CK(cudaMemsetAsync(g.x, 0, N * sizeof(double2), s));
+    nfs::host::GmresResult r;
+    // the Arnoldi vectors have unit norm
+    TRY(nfs::host::gmres(g, gm, tol, 1.0, maxit, r));
+    inner += r.iterations;
+    if (r.status != 0) return NFS_ENOCONV;
+    CK(cudaMemcpyAsync(w, g.x, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    return NFS_OK;
+  }
+};
+
+constexpr int kGmresRestart = 100;
+
+int ensure_nfsep_bases(nfs_ctx* c, int m, int gm) {
+  if (c->zv_cap < m + 1) {
+    if (c->zv) cudaFree(c->zv);
+    c->zv = nullptr;
+    c->zv_cap = 0;
+    TRY(dalloc(c, &c->zv, (size_t)(m + 1) * c->N));
+    c->zv_cap = m + 1;
+  }
+  if (c->gv_cap < gm + 1) {
+    if (c->gv) cudaFree(c->gv);
+    c->gv = nullptr;
+    c->gv_cap = 0;
+    TRY(dalloc(c, &c->gv, (size_t)(gm + 1) * c->N));
+    c->gv_cap = gm + 1;
+  }
+  return ensure_scratch(c, (size_t)kRedBlocks * 2 * (std::max(m, gm) + 2) + 4 * (size_t)(std::max(m, gm) + 2) + 64);
+}
+
+}  // namespace
+
+extern "C" int nfs_setup_biiso(nfs_ctx** out, const int grid[3], const double* lattice, const double k[3],
+                               const nfs_biiso_material* bm, const nfs_options* opt) {
+  if (!out) return NFS_EINVAL;
+  *out = nullptr;
+  if (!grid || !k || !bm || !bm->eps || !bm->gamma) return NFS_EINVAL;
+  for (int l = 0; l < 3; ++l)
+    if (grid[l] <= 0) return NFS_EINVAL;
+  const long long n = (long long)grid[0] * grid[1] * grid[2];
+  // B^{-1} per voxel and component (eq. mtx_B): B_c = i [[zeta, mu], [-eps, -xi]],
+  // xi = chi + i gamma, zeta = chi - i gamma; det B_c = zeta xi - mu eps
+  std::vector<double2> binv((size_t)12 * n);
+  for (int cpt = 0; cpt < 3; ++cpt)
+    for (long long v = 0; v < n; ++v) {
+      const size_t i = (size_t)cpt * n + v;
+      auto cx = [&](const double* a, cplxd dflt) { return a ? cplxd(a[2 * i], a[2 * i + 1]) : dflt; };
+      const cplxd eps = cx(bm->eps, 1.0), mu = cx(bm->mu, 1.0), gam = cx(bm->gamma, 0.0), chi = cx(bm->chi, 0.0);
+      const cplxd I(0.0, 1.0);
+      const cplxd xi = chi + I * gam, zeta = chi - I * gam;
+      const cplxd det = zeta * xi - mu * eps;
+      const double scale = std::abs(zeta) * std::abs(xi) + std::abs(mu) * std::abs(eps);
+      if (!std::isfinite(std::abs(det)) || !(std::abs(det) > 1e-12 * scale)) return NFS_EINVAL;
+      const cplxd inv[4] = {-I * xi / det, -I * mu / det, I * eps / det, I * zeta / det};
+      for (int t = 0; t < 4; ++t) binv[(size_t)(4 * cpt + t) * n + v] = make_double2(inv[t].real(), inv[t].imag());
+    }
+  // the product's tables come from the ordinary set-up with a placeholder
+  // chiral medium (eps = 1, gamma = 0), whose material arrays stay unused
+  std::vector<double> ones((size_t)3 * n, 1.0), zeros((size_t)3 * n, 0.0);
+  nfs_material placeholder{};
+  placeholder.kind = NFS_MEDIUM_CHIRAL;
+  placeholder.axis_a = 0;
+  placeholder.axis_b = 1;
+  placeholder.eps = ones.data();
+  placeholder.mu = nullptr;
+  placeholder.gamma = zeros.data();
+  nfs_ctx* c = nullptr;
+  TRY(nfs_setup(&c, grid, lattice, k, &placeholder, opt));
+  const int rc = [&]() -> int {
+    TRY(dalloc(c, &c->binv64, binv.size()));
+    CK(cudaMemcpy(c->binv64, binv.data(), binv.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(nfs::nfsep_prepare(c->n3));
+    return NFS_OK;
+  }();
+  if (rc != NFS_OK) {
+    nfs_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return NFS_OK;
+}
+
+extern "C" int nfs_nfsep_matvec(nfs_ctx* c, const void* y, void* My) {
+  if (!c || !y || !My || y == My) return NFS_EINVAL;
+  if (!c->binv64) return NFS_EUNSUPPORTED;
+  if (((uintptr_t)y | (uintptr_t)My) & 15) return NFS_EINVAL;
+  return nfsep_apply(c, c->stream, (const double2*)y, (double2*)My, nullptr, make_double2(0.0, 0.0));
+}
+
+extern "C" int nfs_nfsep_eigs(nfs_ctx* c, int nev, const double sigma[2], double* omega, void* Y,
+                              nfs_nfsep_info* info) {
+  if (!c || !sigma || !omega || nev <= 0) return NFS_EINVAL;
+  if (!c->binv64) return NFS_EUNSUPPORTED;
+  if (!(std::isfinite(sigma[0]) && std::isfinite(sigma[1]))) return NFS_EINVAL;
+  int m = c->opt.ncv > 0 ? c->opt.ncv : std::max(2 * nev + 2, 20);
+  m = (int)std::min<long long>(m, c->N - 1);
+  if (m < nev + 2) return NFS_EINVAL;
+  const int gm = (int)std::min<long long>(kGmresRestart, c->N - 1);
+  TRY(ensure_nfsep_bases(c, m, gm));
+  const double2 sg = make_double2(sigma[0], sigma[1]);
+  const long long launches_0 = c->launches;
+  // start vector
+  nfs::k_random_fill<<<grid_blocks(c->N, 256), 256, 0, c->stream>>>(c->zv, c->N, 0, 1, c->opt.seed);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  DevGmres g(c, c->gv, c->r64, c->x64, sg);
+  DevShiftInvert op(c, c->zv, c->p64, g, gm, c->opt.cg_tol, c->opt.cg_maxit);
+  nfs::host::ArnoldiResult r;
+  const int rc = nfs::host::krylov_schur(op, nev, m, c->opt.eig_tol, c->opt.max_restarts, r);
+  if (rc != NFS_OK) return rc;
+  for (int e = 0; e < nev; ++e) {
+    const cplxd lam = cplxd(sigma[0], sigma[1]) + 1.0 / r.theta[e];
+    omega[2 * e] = lam.real();
+    omega[2 * e + 1] = lam.imag();
+  }
+  if (Y) CK(cudaMemcpyAsync(Y, c->zv, (size_t)nev * c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (info) {
+    info->arnoldi_steps = r.steps;
+    info->restarts = r.restarts;
+    info->gmres_iterations = op.inner;
+    info->nconv = r.nconv;
+    info->max_ritz_residual = r.max_residual;
+    info->status = r.status;
+    info->kernel_launches = c->launches - launches_0;
+  }
+  return r.status;
+}
+
+extern "C" int nfs_nfsep_fields(nfs_ctx* c, int m, const void* Yv, void* Xv) {
+  if (!c || m <= 0 || !Yv || !Xv) return NFS_EINVAL;
+  if (!c->binv64) return NFS_EUNSUPPORTED;
+  if ((((uintptr_t)Yv) | ((uintptr_t)Xv)) & 15) return NFS_EINVAL;
+  const long long n = c->n, N = c->N;
+  for (int j = 0; j < m; ++j) {
+    // Algorithm 1, second branch: y <- Sigma^{1/2} y, x = B^{-1} diag(P_r, Q_r) y
+    cudaError_t e = nfs::nfsep_prescale((const double2*)Yv + (long long)j * N, c->t64, c->lam64, c->n1, c->n2,
+                                        c->n3, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "nfsep fields prescale");
+    nfs::MatvecArgs<double> a = margs<double>(c, c->t64, nullptr, nullptr);
+    e = nfs::pass1_launch<double>(a);
+    if (e != cudaSuccess) return cuda_fail(e, "nfsep fields pass 1");
+    e = nfs::nfsep_fields((const double2*)c->fld, c->binv64, c->tw64[2], c->bloch64, c->n1, c->n2, c->n3,
+                          (double2*)Xv + (long long)j * 6 * n, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "nfsep fields");
+    c->launches += 3;
   }
   return NFS_OK;
 }

@@ -1,0 +1,43 @@
+// Device pieces of the null space free standard problem for any nonsingular
+// B (eq. NFSEP_org, Algorithm 1's second branch), complex128 (nfsep.cu):
+//
+//   M y = [Sigma_r^{1/2} Q_r^* e ; Sigma_r^{1/2} P_r^* h],
+//   [e; h] = B^{-1} [P_r Sigma_r^{1/2} y1 ; Q_r Sigma_r^{1/2} y2],
+//
+// run as: nfsep_prescale (Sigma_r^{1/2}), pass 1 of the A_r product
+// (assembly, inverse DFTs along x and y), nfsep_pass2 (inverse DFT along z,
+// B^{-1} per voxel with h into fields 0-2 and e into fields 3-5, forward DFT
+// along z), pass 3 of the A_r product (which then yields [P_r^* h; Q_r^* e])
+// and nfsep_post (the two halves exchanged, Sigma_r^{1/2}, optionally minus
+// sigma y).  B^{-1} is stored per voxel and component as the 2 x 2 block
+// coupling (p_c, q_c) to (e_c, h_c): binv[(4 c + t) n + v], t = 00, 01, 10, 11.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace nfs {
+
+// t = Sigma_r^{1/2} y: each quarter times Lambda_q^{1/4} at its index
+cudaError_t nfsep_prescale(const double2* y, double2* t, const double2* lam, int n1, int n2, int n3,
+                           cudaStream_t s);
+// out = [Sigma^{1/2} a_2; Sigma^{1/2} a_1] - sigma v (quarters: out_0 from a_2,
+// out_1 from a_3, out_2 from a_0, out_3 from a_1); v may be nullptr
+cudaError_t nfsep_post(const double2* a, double2* out, const double2* lam, int n1, int n2, int n3,
+                       const double2* v, double2 sigma, cudaStream_t s);
+cudaError_t nfsep_prepare(int n3);
+cudaError_t nfsep_pass2(double2* fld, const double2* binv, const double2* tw3, int n1, int n2, int n3,
+                        cudaStream_t s);
+// Algorithm 1 (second branch): X = [E; H] = D [e; h] / sqrt(n) from the pass-1
+// fields of Sigma_r^{1/2} y (D: the Bloch twist, from its three 1-D diagonals)
+cudaError_t nfsep_fields(const double2* fld, const double2* binv, const double2* tw3, const double2* bloch,
+                         int n1, int n2, int n3, double2* X, cudaStream_t s);
+
+// Long-vector operations of the Krylov drivers (complex128):
+// w -= sign * sum_{j<m} c_j V_j, c device interleaved complex, V_j at V + j N
+cudaError_t zaxpy_basis(double2* w, const double2* V, long long N, const double* c, int m, double sign,
+                        cudaStream_t s);
+// dst = scale * src
+cudaError_t zscale_copy(const double2* src, double2* dst, double scale, long long N, cudaStream_t s);
+// V_i <- sum_{r<m} V_r Y[r k + i], i < k, in place (Y device interleaved complex)
+cudaError_t zrotate(double2* V, int m, const double* Y, int k, long long N, cudaStream_t s);
+
+}  // namespace nfs

@@ -45,6 +45,8 @@ EXPORTED = (
     "nfs_eigs", "nfs_eig_grad", "nfs_num_voxels", "nfs_device_bytes", "nfs_set_stream",
     "nfs_destroy", "nfs_strerror", "nfs_matvec_noalloc",
     "nfs_setup_batch", "nfs_eigs_batch", "nfs_batch_num_classes", "nfs_destroy_batch",
+    "nfs_eig_fields", "nfs_gep_residual", "nfs_band_structure",
+    "nfs_setup_biiso", "nfs_nfsep_matvec", "nfs_nfsep_eigs", "nfs_nfsep_fields",
 )
 NOALLOC_MAX_VOXELS = 32768
 
@@ -121,6 +123,27 @@ class EigsInfo(ctypes.Structure):
     ]
 
 
+class BiisoMaterial(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.POINTER(ctypes.c_double)),
+        ("mu", ctypes.POINTER(ctypes.c_double)),
+        ("gamma", ctypes.POINTER(ctypes.c_double)),
+        ("chi", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class NfsepInfo(ctypes.Structure):
+    _fields_ = [
+        ("arnoldi_steps", ctypes.c_int),
+        ("restarts", ctypes.c_int),
+        ("gmres_iterations", ctypes.c_longlong),
+        ("nconv", ctypes.c_int),
+        ("max_ritz_residual", ctypes.c_double),
+        ("status", ctypes.c_int),
+        ("kernel_launches", ctypes.c_longlong),
+    ]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [
         ("grid", ctypes.c_int * 3),
@@ -163,6 +186,17 @@ def lib():
     L.nfs_eig_fields.restype = ip
     L.nfs_gep_residual.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(ctypes.c_double)]
     L.nfs_gep_residual.restype = ip
+    L.nfs_setup_biiso.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(BiisoMaterial),
+                                  ctypes.POINTER(Options)]
+    L.nfs_setup_biiso.restype = ip
+    L.nfs_nfsep_matvec.argtypes = [vp, vp, vp]
+    L.nfs_nfsep_matvec.restype = ip
+    L.nfs_nfsep_eigs.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp,
+                                 ctypes.POINTER(NfsepInfo)]
+    L.nfs_nfsep_eigs.restype = ip
+    L.nfs_nfsep_fields.argtypes = [vp, ip, vp, vp]
+    L.nfs_nfsep_fields.restype = ip
     L.nfs_num_voxels.argtypes = [vp]
     L.nfs_num_voxels.restype = ctypes.c_longlong
     L.nfs_device_bytes.argtypes = [vp]
@@ -400,6 +434,96 @@ class Context:
         _check(lib().nfs_gep_residual(self.h, m, _dptr(om), ctypes.c_void_p(X.data_ptr()), _dptr(res)),
                "nfs_gep_residual")
         return res
+
+
+class NFSEPContext:
+    """A bi-isotropic medium outside the Assumption (nfs_setup_biiso): the
+    null space free standard problem M y = omega y of eq. NFSEP_org, its
+    shift-and-invert Arnoldi eigensolve and Algorithm 1's second branch."""
+
+    def __init__(self, grid, kdota, medium, stream=None, **opts):
+        import torch
+        L = lib()
+        if medium.kind != "biisotropic":
+            raise ValueError("NFSEPContext takes a biisotropic medium")
+        self.grid = tuple(int(g) for g in grid)
+        n1, n2, n3 = self.grid
+        self.n = n1 * n2 * n3
+        self.N = 4 * self.n
+
+        def carr(a):
+            return None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+        self._keep = [carr(medium.eps), carr(medium.mu), carr(medium.gamma), carr(getattr(medium, "chi", None))]
+        m = BiisoMaterial()
+        null = ctypes.POINTER(ctypes.c_double)()
+        for name, arr in zip(("eps", "mu", "gamma", "chi"), self._keep):
+            setattr(m, name, arr.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                    if arr is not None else null)
+        o = default_options()
+        for key, val in opts.items():
+            setattr(o, key, val)
+        o.stream = stream if stream is not None else _current_stream()
+        a = float(getattr(medium, "a", 1.0))
+        lattice = np.diag([a, a, a]).astype(np.float64).ravel()
+        kvec = np.asarray(kdota, dtype=np.float64) / a
+        g = (ctypes.c_int * 3)(*self.grid)
+        h = ctypes.c_void_p()
+        _check(L.nfs_setup_biiso(ctypes.byref(h), g, _dptr(lattice), _dptr(kvec), ctypes.byref(m), ctypes.byref(o)),
+               "nfs_setup_biiso")
+        self.h = h
+        self._torch = torch
+
+    def _vec(self, t):
+        torch = self._torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()
+                and t.numel() == self.N):
+            raise ValueError(f"expected a contiguous CUDA complex128 tensor of {self.N} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def matvec(self, y, out=None):
+        """M y (eq. NFSEP_org)."""
+        if out is None:
+            out = self._torch.empty_like(y)
+        _check(lib().nfs_nfsep_matvec(self.h, self._vec(y), self._vec(out)), "nfs_nfsep_matvec")
+        return out
+
+    def eigs(self, nev, sigma, vectors=True, allow_noconv=False):
+        """The nev eigenvalues of M nearest the complex shift sigma: (omega
+        complex (nev,), Y (nev, 4n) or None, NfsepInfo)."""
+        torch = self._torch
+        sg = np.array([complex(sigma).real, complex(sigma).imag], dtype=np.float64)
+        om = np.zeros(2 * nev, dtype=np.float64)
+        Y = torch.empty((nev, self.N), dtype=torch.complex128, device="cuda") if vectors else None
+        info = NfsepInfo()
+        code = lib().nfs_nfsep_eigs(self.h, int(nev), _dptr(sg), _dptr(om),
+                                    ctypes.c_void_p(Y.data_ptr()) if vectors else None, ctypes.byref(info))
+        if code != NFS_OK and not (allow_noconv and code == NFS_ENOCONV):
+            raise NFSError(code, "nfs_nfsep_eigs")
+        return om[0::2] + 1j * om[1::2], Y, info
+
+    def fields(self, Y):
+        """[E; H] of NFSEP eigenvectors Y (m, 4n): (m, 6, n3, n2, n1)."""
+        torch = self._torch
+        Y = Y.reshape(-1, self.N)
+        if not (Y.is_cuda and Y.dtype == torch.complex128 and Y.is_contiguous()):
+            raise ValueError("Y must be a contiguous CUDA complex128 tensor (m, 4n)")
+        m = int(Y.shape[0])
+        n1, n2, n3 = self.grid
+        X = torch.empty((m, 6, n3, n2, n1), dtype=torch.complex128, device="cuda")
+        _check(lib().nfs_nfsep_fields(self.h, m, ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(X.data_ptr())),
+               "nfs_nfsep_fields")
+        return X
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().nfs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import workloads as wl  # noqa: E402
-from oracle import gep, nfgep  # noqa: E402
+from oracle import gep, nfgep, nfsep  # noqa: E402
 
 
 def write(name, header, values):
@@ -75,6 +75,22 @@ oracle tier O1: dense Hermitian-definite pencil (oracle.gep.dense_eigs), FP64
 """)
         for r in rows:
             f.write(f"{r[0]:d} {r[1]:.17e} {r[2]:.17e} {r[3]:.17e}\n")
+
+    # nfsep8: the four eigenvalues nearest sigma = 2 + 0.1i of the null space
+    # free standard problem (thm:nfep, eq. NFSEP_org) of a lossy bi-isotropic
+    # sphere, 8^3, k.a = (0.1, 0.2, 0.3): oracle shift-and-invert Arnoldi
+    g = (8, 8, 8)
+    med = wl.biisotropic_sphere(g, 0.25, 13.0 + 2.0j, 1.0, 0.5, 0.2)
+    om, _ = nfsep.NFSEP(g, (0.1, 0.2, 0.3), med).eigs_near(2.0 + 0.1j, 4)
+    with open(os.path.join(HERE, "nfsep8_omega.txt"), "w") as f:
+        f.write("""# 4 eigenvalues nearest sigma = 2 + 0.1i of M y = omega y (eq. NFSEP_org; thm:nfep: the GEP's
+# nonzero eigenvalues) for a bi-isotropic sphere outside the Assumption: radius 0.25, inside
+# eps = 13 + 2i, gamma = 0.5, chi = 0.2, mu = 1; outside vacuum; grid 8x8x8, k.a = (0.1, 0.2, 0.3)
+# oracle: FFT NFSEP operator, shift-and-invert Arnoldi with GMRES (oracle.nfsep.NFSEP.eigs_near), FP64
+# columns: re, im (nearest sigma first)
+""")
+        for w in om:
+            f.write(f"{w.real:.17e} {w.imag:.17e}\n")
 
 
 if __name__ == "__main__":

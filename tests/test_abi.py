@@ -52,6 +52,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(nfs_options), sizeof(nfs_material), sizeof(nfs_solve_info), sizeof(nfs_eigs_info));
   printf("%zu %zu %zu\n", offsetof(nfs_options, seed), offsetof(nfs_options, stream), offsetof(nfs_eigs_info, max_ritz_residual));
   printf("%zu %zu %zu\n", sizeof(nfs_problem), offsetof(nfs_problem, k), offsetof(nfs_problem, mat));
+  printf("%zu %zu %zu %zu\n", sizeof(nfs_biiso_material), sizeof(nfs_nfsep_info),
+         offsetof(nfs_nfsep_info, max_ritz_residual), offsetof(nfs_nfsep_info, kernel_launches));
   return 0;
 }
 """
@@ -72,6 +74,10 @@ int main(void) {
     assert sizes[7] == ctypes.sizeof(nfs.Problem)
     assert sizes[8] == nfs.Problem.k.offset
     assert sizes[9] == nfs.Problem.mat.offset
+    assert sizes[10] == ctypes.sizeof(nfs.BiisoMaterial)
+    assert sizes[11] == ctypes.sizeof(nfs.NfsepInfo)
+    assert sizes[12] == nfs.NfsepInfo.max_ritz_residual.offset
+    assert sizes[13] == nfs.NfsepInfo.kernel_launches.offset
 
 
 def test_default_options(nfs):
