@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--skip-grad", action="store_true", help="skip the eigenvalue-gradient (field64) leg")
     p.add_argument("--skip-bands", action="store_true", help="skip the band-structure (bands48) leg")
     p.add_argument("--skip-mesh", action="store_true", help="skip the mesh-convergence (8^3 .. 128^3) leg")
+    p.add_argument("--skip-nfsep", action="store_true",
+                   help="skip the leg for media outside the Assumption (NFSEP, shift-and-invert Arnoldi)")
     p.add_argument("--skip-fields", action="store_true",
                    help="skip the eigenvector-fields leg (E, H of the headline eigenpairs and their GEP residuals)")
     p.add_argument("--matvec-only", action="store_true",
@@ -387,6 +389,32 @@ def mesh_leg(nfs, wl, torch):
             "grids": out}
 
 
+def nfsep_leg(nfs, wl, torch):
+    """nfsep16: media outside the Assumption (eq. NFSEP_org, Algorithm 1's
+    second branch): the four eigenvalues nearest 2 + 0.1i of a lossy
+    bi-isotropic sphere on 16^3 by shift-and-invert Arnoldi with GMRES
+    (complex128; the unpreconditioned inner solves dominate).  A failure is
+    reported in the line instead of ending the run."""
+    g = (16, 16, 16)
+    med = wl.biisotropic_sphere(g, 0.25, 13.0 + 2.0j, 1.0, 0.5, 0.2)
+    try:
+        ctx = nfs.NFSEPContext(g, (0.1, 0.2, 0.3), med, eig_tol=1e-10, cg_tol=1e-12, cg_maxit=8000, max_restarts=20)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        om, _, info = ctx.eigs(4, 2.0 + 0.1j, vectors=False, allow_noconv=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        ctx.close()
+    except Exception as e:  # noqa: BLE001 -- recorded, the other legs stand
+        return {"error": str(e)}
+    return {"workload": "nfsep16: 16^3 bi-isotropic sphere r=0.25 (eps 13+2i, gamma 0.5, chi 0.2), "
+                        "k.a=(0.1,0.2,0.3), 4 eigenvalues nearest 2+0.1i, complex128",
+            "seconds": dt, "omega": [[float(w.real), float(w.imag)] for w in om],
+            "arnoldi_steps": info.arnoldi_steps, "restarts": info.restarts,
+            "gmres_iterations": int(info.gmres_iterations), "nconv": info.nconv, "status": info.status,
+            "products_per_s": int(info.gmres_iterations) / dt}
+
+
 def fields_leg(ctx, omega, Y, n, torch, hbm):
     """Algorithm 1's final step on the headline eigenpairs: the fields
     [E; H] = B^{-1} diag(P_r, Q_r) y of all NEV eigenvectors (nfs_eig_fields,
@@ -566,6 +594,7 @@ def run_ours(args):
     grad = None if (args.skip_grad or rank != 0) else grad_leg(nfs, wl, torch, np)
     bands = None if (args.skip_bands or rank != 0) else bands_leg(nfs, wl, torch)
     mesh = None if (args.skip_mesh or rank != 0) else mesh_leg(nfs, wl, torch)
+    nfsep_r = None if (args.skip_nfsep or rank != 0) else nfsep_leg(nfs, wl, torch)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
@@ -604,6 +633,7 @@ def run_ours(args):
         "fields": fields,
         "bands": bands,
         "mesh": mesh,
+        "nfsep": nfsep_r,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
