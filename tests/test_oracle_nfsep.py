@@ -112,3 +112,29 @@ def test_vacuum_closed_form():
                    + 4 * np.sin(np.pi * (i3 + K[2]) / n3) ** 2 * n3 ** 2).ravel()
     ref = np.concatenate([disp, disp, -disp, -disp])
     assert match(w, ref) < 1e-10 * disp.max()
+
+
+def test_both_branches_of_algorithm_1_give_the_same_fields():
+    """Inside the Assumption both branches of Algorithm 1 apply: the fields
+    B^{-1} diag(P_r, Q_r) y_r of an HHPD-NFGEP eigenvector and B^{-1}
+    diag(P_r, Q_r) Sigma^{1/2} y of the NFSEP eigenvector of the same simple
+    eigenvalue are parallel."""
+    med = wl.chiral_sphere(GRID, 0.3, 13.0, 1.0, 0.5)
+    nh = nfgep.NFGEP(GRID, K, med)
+    th, Yr = sla.eigh(nh.dense_Br(), nh.dense_Ar())
+    ns = nfsep.NFSEP(GRID, K, med)
+    w, V = np.linalg.eig(ns.dense())
+    om = 1.0 / th
+    checked = 0
+    for j in np.argsort(np.abs(om))[:10]:
+        gaps = np.abs(om - om[j])
+        if np.sort(gaps)[1] < 1e-6 * abs(om[j]):
+            continue  # degenerate: no unique direction
+        i = int(np.argmin(np.abs(w - om[j])))
+        assert abs(w[i] - om[j]) < 1e-9 * abs(om[j])
+        x1 = nh.eigvec_fields(Yr[:, j]).ravel()
+        x2 = ns.fields(V[:, i]).ravel()
+        cos = abs(np.vdot(x1, x2)) / (np.linalg.norm(x1) * np.linalg.norm(x2))
+        assert cos > 1 - 1e-9
+        checked += 1
+    assert checked >= 4
