@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--skip-bands", action="store_true", help="skip the band-structure (bands48) leg")
     p.add_argument("--skip-mesh", action="store_true", help="skip the mesh-convergence (8^3 .. 128^3) leg")
     p.add_argument("--skip-nfsep", action="store_true",
-                   help="skip the leg for media outside the Assumption (NFSEP, shift-and-invert Arnoldi)")
+                   help="skip the leg for media outside the Assumption (NFSEP at 8^3, shift-and-invert Arnoldi)")
     p.add_argument("--skip-fields", action="store_true",
                    help="skip the eigenvector-fields leg (E, H of the headline eigenpairs and their GEP residuals)")
     p.add_argument("--matvec-only", action="store_true",
@@ -390,12 +390,12 @@ def mesh_leg(nfs, wl, torch):
 
 
 def nfsep_leg(nfs, wl, torch):
-    """nfsep16: media outside the Assumption (eq. NFSEP_org, Algorithm 1's
+    """nfsep8: media outside the Assumption (eq. NFSEP_org, Algorithm 1's
     second branch): the four eigenvalues nearest 2 + 0.1i of a lossy
-    bi-isotropic sphere on 16^3 by shift-and-invert Arnoldi with GMRES
+    bi-isotropic sphere on 8^3 by shift-and-invert Arnoldi with GMRES
     (complex128; the unpreconditioned inner solves dominate).  A failure is
     reported in the line instead of ending the run."""
-    g = (16, 16, 16)
+    g = (8, 8, 8)
     med = wl.biisotropic_sphere(g, 0.25, 13.0 + 2.0j, 1.0, 0.5, 0.2)
     try:
         ctx = nfs.NFSEPContext(g, (0.1, 0.2, 0.3), med, eig_tol=1e-10, cg_tol=1e-12, cg_maxit=8000, max_restarts=20)
@@ -407,7 +407,7 @@ def nfsep_leg(nfs, wl, torch):
         ctx.close()
     except Exception as e:  # noqa: BLE001 -- recorded, the other legs stand
         return {"error": str(e)}
-    return {"workload": "nfsep16: 16^3 bi-isotropic sphere r=0.25 (eps 13+2i, gamma 0.5, chi 0.2), "
+    return {"workload": "nfsep8: 8^3 bi-isotropic sphere r=0.25 (eps 13+2i, gamma 0.5, chi 0.2), "
                         "k.a=(0.1,0.2,0.3), 4 eigenvalues nearest 2+0.1i, complex128",
             "seconds": dt, "omega": [[float(w.real), float(w.imag)] for w in om],
             "arnoldi_steps": info.arnoldi_steps, "restarts": info.restarts,
