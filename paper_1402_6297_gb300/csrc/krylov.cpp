@@ -130,15 +130,36 @@ int krylov_schur(KrylovOps& ops, int nev, int m, double tol, int max_restarts, A
   auto Sx = [&](int r, int c) -> cplxd& { return S[(size_t)r * m + c]; };
   const int keep = std::max(nev + 1, std::min(m - 1, nev + (m - nev) / 2));
   int k0 = 0;
+  unsigned long long injections = 0;
   for (;;) {
     for (int j = k0; j < m; ++j) {
       KRY_TRY(ops.apply(j));
       ++res.steps;
       KRY_TRY(orthogonalise(ops, j + 1, col));
-      for (int i = 0; i <= j; ++i) Sx(i, j) = col[i];
+      double colnorm = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        Sx(i, j) = col[i];
+        colnorm += std::norm(col[i]);
+      }
       double h = 0.0;
       KRY_TRY(ops.norm(h));
-      if (!(h > 0.0)) return kBreakdown;
+      if (!(h == h)) return kBreakdown;  // NaN
+      colnorm = std::sqrt(colnorm + h * h);
+      if (!(h > 1e-13 * colnorm)) {
+        // invariant subspace: continue from a random direction orthogonal to
+        // the basis, uncoupled (S(j+1, j) = 0)
+        KRY_TRY(ops.random(0x9E3779B97F4A7C15ull * ++injections + 12345));
+        ++res.injections;
+        std::vector<cplxd> discard;
+        KRY_TRY(orthogonalise(ops, j + 1, discard));
+        KRY_TRY(orthogonalise(ops, j + 1, discard));
+        double r = 0.0;
+        KRY_TRY(ops.norm(r));
+        if (!(r > 0.0)) return kBreakdown;
+        Sx(j + 1, j) = 0.0;
+        KRY_TRY(ops.store(j + 1, 1.0 / r));
+        continue;
+      }
       Sx(j + 1, j) = h;
       KRY_TRY(ops.store(j + 1, 1.0 / h));
     }

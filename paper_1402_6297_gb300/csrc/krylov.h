@@ -28,6 +28,8 @@ struct KrylovOps {
   virtual int rotate(int m, const std::vector<cplxd>& Q, int k) = 0;
   virtual int copy(int dst, int src) = 0;                         // V_dst = V_src
   virtual int load(int j) = 0;                                    // w = V_j
+  // w = a random vector (counter-based, from seed)
+  virtual int random(unsigned long long seed) = 0;
 };
 
 // Operations GMRES needs beyond the basis: the right-hand side, the
@@ -56,6 +58,7 @@ struct ArnoldiResult {
   int restarts = 0;
   int nconv = 0;
   double max_residual = 0.0; // max |h_{m+1,m} s_m| / |theta| over the nev
+  int injections = 0;        // random directions taken at invariant subspaces
   int status = 0;            // 0 or NFS_ENOCONV (-6)
 };
 
@@ -63,7 +66,10 @@ struct ArnoldiResult {
 // (Op = (M - sigma I)^{-1}: the eigenvalues of M nearest sigma).  V_0 must
 // hold a start vector on entry.  Basis size m (nev + 2 <= m < cap); on
 // return V_0 .. V_{nev-1} hold unit eigenvectors of the nev values, in the
-// order of res.theta (largest modulus first).
+// order of res.theta (largest modulus first).  When the Krylov space becomes
+// invariant (h_{j+1,j} at round-off) the next basis vector is a random one
+// orthogonalised against the basis, with zero coupling: the Ritz values so
+// far are then exact and the search goes on in the complement.
 int krylov_schur(KrylovOps& ops, int nev, int m, double tol, int max_restarts, ArnoldiResult& res);
 
 }  // namespace host

@@ -1707,6 +1707,12 @@ struct DevBasis : virtual nfs::host::KrylovOps {
     CK(cudaMemcpyAsync(w, V + (long long)j * N, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     return NFS_OK;
   }
+  int random(unsigned long long seed) override {
+    nfs::k_random_fill<<<grid_blocks(N, 256), 256, 0, s>>>(w, N, 0, 1, seed);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    return NFS_OK;
+  }
 };
 
 // GMRES on (M - sigma I) x = b

@@ -65,6 +65,12 @@ struct DenseBasis : virtual nfs::host::KrylovOps {
   }
   int copy(int dst, int src) override { V[dst] = V[src]; return 0; }
   int load(int j) override { w = V[j]; return 0; }
+  int random(unsigned long long seed) override {
+    std::mt19937_64 rng(seed);
+    std::normal_distribution<double> nd;
+    for (int r = 0; r < N; ++r) w[r] = cplxd(nd(rng), nd(rng));
+    return 0;
+  }
 };
 
 struct DenseGmres : DenseBasis, nfs::host::GmresOps {
@@ -150,6 +156,21 @@ extern "C" int shim_krylov_schur(int N, const double* A, int nev, int m, double 
     }
   *steps = r.steps;
   *restarts = r.restarts;
+  return r.status;
+}
+
+// as shim_krylov_schur from a given start vector v0
+extern "C" int shim_krylov_schur_from(int N, const double* A, const double* v0, int nev, int m, double tol,
+                                      int max_restarts, double* theta, int* steps, int* injections) {
+  const Vec a = load((size_t)N * N, A);
+  DenseBasis ops(N, &a, 0.0, m + 1);
+  ops.V[0] = load(N, v0);
+  nfs::host::ArnoldiResult r;
+  const int rc = nfs::host::krylov_schur(ops, nev, m, tol, max_restarts, r);
+  if (rc != 0) return rc;
+  out_vec(r.theta, theta);
+  *steps = r.steps;
+  *injections = r.injections;
   return r.status;
 }
 

@@ -34,6 +34,7 @@ def kl():
     L.shim_gmres.argtypes = [i_, P, d_, d_, P, P, i_, d_, i_, IP, P]
     L.shim_krylov_schur.argtypes = [i_, P, i_, i_, d_, i_, ctypes.c_uint, P, P, IP, IP]
     L.shim_shift_invert.argtypes = [i_, P, d_, d_, i_, i_, d_, i_, d_, ctypes.c_uint, P, IP, IP]
+    L.shim_krylov_schur_from.argtypes = [i_, P, P, i_, i_, d_, i_, P, IP, IP]
     return L
 
 
@@ -113,3 +114,31 @@ def test_shift_invert_on_the_oracle_nfsep(kl):
     ref = w[np.argsort(np.abs(w - sigma))[:nev]]
     assert match(lc, ref) < 1e-9 * np.abs(ref).max()
     assert inner.value > steps.value
+
+
+def test_krylov_schur_leaves_an_invariant_subspace(kl):
+    """A start vector inside an invariant subspace (the first block of a
+    block-diagonal matrix) makes h_{j+1,j} vanish after a few steps; the
+    driver continues from a random direction and still finds the eigenvalues
+    of largest modulus, which all lie in the other block."""
+    rng = np.random.default_rng(4)
+    k, N = 6, 120
+    A = np.zeros((N, N), complex)
+    A[:k, :k] = 0.3 * (rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k)))
+    B = (rng.standard_normal((N - k, N - k)) + 1j * rng.standard_normal((N - k, N - k))) / np.sqrt(N)
+    B[np.arange(4), np.arange(4)] += np.array([5.0, -4.5, 4.0j, 3.5])
+    A[k:, k:] = B
+    v0 = np.zeros(N, complex)
+    v0[:k] = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    Ac, Ap = cp(A)
+    vc, vp = cp(v0)
+    nev = 4
+    th = np.zeros(nev, complex)
+    thc, thp = cp(th)
+    steps, inj = ctypes.c_int(), ctypes.c_int()
+    rc = kl.shim_krylov_schur_from(N, Ap, vp, nev, 24, 1e-12, 100, thp, ctypes.byref(steps), ctypes.byref(inj))
+    assert rc == 0
+    assert inj.value >= 1
+    ev = np.linalg.eigvals(A)
+    ref = ev[np.argsort(-np.abs(ev))[:nev]]
+    assert match(thc, ref) < 1e-10
