@@ -199,3 +199,44 @@ def test_kpath_samples_segment_midpoints():
     assert np.min(np.linalg.norm(ks[:, None, :] - corners[None], axis=2)) > 0.02
     ks2, _ = nfs.kpath(("X", (0.5, 0.5, 0.5)), per_segment=4)
     assert np.allclose(ks2[:, 0], 0.5) and np.allclose(ks2[:, 1], ks2[:, 2])
+
+
+def test_new_entry_points_validate_on_the_host(nfs):
+    """Field recovery, GEP residual, band structure and the NFSEP calls reject
+    bad arguments before any CUDA call; a singular B (mu eps = zeta xi in some
+    voxel, eq. mtx_B) is refused by nfs_setup_biiso."""
+    L = nfs.lib()
+    assert L.nfs_eig_fields(None, 1, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_gep_residual(None, 1, None, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_nfsep_matvec(None, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_nfsep_eigs(None, 2, None, None, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_nfsep_fields(None, 1, None, None) == nfs.NFS_EINVAL
+    g = (8, 8, 8)
+    med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+    m, keep = nfs._material(med)
+    gi = (ctypes.c_int * 3)(*g)
+    k = np.array([[0.1, 0.2, 0.3]])
+    om = np.zeros(4)
+    assert L.nfs_band_structure(gi, ctypes.byref(m), 0, nfs._dptr(k), None, 4, 0, nfs._dptr(om), None, None) \
+        == nfs.NFS_EINVAL
+    assert L.nfs_band_structure(gi, ctypes.byref(m), 1, nfs._dptr(k), None, 0, 0, nfs._dptr(om), None, None) \
+        == nfs.NFS_EINVAL
+    o = nfs.default_options()
+    o.deflation_checks = -1
+    assert L.nfs_band_structure(gi, ctypes.byref(m), 1, nfs._dptr(k), ctypes.byref(o), 4, 0, nfs._dptr(om),
+                                None, None) == nfs.NFS_EINVAL
+    # singular B: chi = 1 with eps = mu = 1, gamma = 0 gives zeta xi = mu eps
+    sing = wl.biisotropic_sphere(g, 0.25, 1.0, 1.0, 0.0, 1.0)
+    arrs = [np.ascontiguousarray(a, dtype=np.complex128) for a in (sing.eps, sing.mu, sing.gamma, sing.chi)]
+    bm = nfs.BiisoMaterial()
+    for name, a in zip(("eps", "mu", "gamma", "chi"), arrs):
+        setattr(bm, name, a.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    h = ctypes.c_void_p()
+    kv = np.array([0.1, 0.2, 0.3])
+    assert L.nfs_setup_biiso(ctypes.byref(h), gi, None, nfs._dptr(kv), ctypes.byref(bm), None) == nfs.NFS_EINVAL
+    assert not h.value
+    # the binding refuses media the library does not solve
+    with pytest.raises(ValueError):
+        nfs._material(wl.biisotropic_sphere(g, 0.25, 13.0 + 1j, 1.0, 0.5, 0.0))
+    with pytest.raises(ValueError):
+        nfs.NFSEPContext(g, (0.1, 0.2, 0.3), med)
