@@ -42,6 +42,7 @@ KNOBS = {
     "NFS_Z_MINB": [3, 2],
     "NFS_ZTILE_C64": [16, 8],
     "NFS_C64_PAIRS": [0, 1],
+    "NFS_PASS1_FUSED_LOAD": [0, 1],
 }
 MIN_GAIN = 0.03  # relative improvement a knob change must show to be taken
 

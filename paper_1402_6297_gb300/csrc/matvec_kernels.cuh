@@ -198,6 +198,12 @@ struct Stage {
   }
 };
 
+// Pass 1's input handling: 0 loads every input block first (all loads in
+// flight together), 1 handles one block at a time (fewer live registers).
+#ifndef NFS_PASS1_FUSED_LOAD
+#define NFS_PASS1_FUSED_LOAD 0
+#endif
+
 template <typename R, int NX, int NY, int NT, int MINB>
 __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
@@ -239,6 +245,66 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
   constexpr int NVMAX = (NE / 3 + 2) / EPV;
   constexpr int PER = (NVMAX + NT - 1) / NT;
   const int nv = (e1 - e0) / EPV;
+#if NFS_PASS1_FUSED_LOAD
+  // one block of inputs at a time: load, CG update, assembly and staging, so
+  // that only one block's inputs are live (no register spills at 96 x 96
+  // with three CTAs per SM)
+  const C a3 = lam[NX + NY + i3];
+  using SG = Stage<NX, NY>;
+  const int sb1 = SG::base(rank, 1), sb2 = SG::base(rank, 2);
+  const int r1 = rank == 2 ? 0 : rank + 1, r2 = rank == 0 ? 2 : rank - 1;
+  const R bt = cg_r != nullptr ? (R)*cg_beta : (R)0;
+  const long long goff = (2 * grp) * n + (long long)i3 * NE + e0;
+#pragma unroll
+  for (int b = 0; b < PER; ++b) {
+    const int v = b * NT + (int)threadIdx.x;
+    if (v < nv) {
+      V ra = reinterpret_cast<const V*>(ua)[v];
+      V rb = reinterpret_cast<const V*>(ub)[v];
+      if (cg_r != nullptr) {
+        // CG direction update fused into the load: u = r + beta u, stored back
+        const V qa = ldg_c(reinterpret_cast<const V*>(cg_r + goff) + v);
+        const V qb = ldg_c(reinterpret_cast<const V*>(cg_r + goff + n) + v);
+        if constexpr (EPV == 2) {
+          ra = make_float4(qa.x + bt * ra.x, qa.y + bt * ra.y, qa.z + bt * ra.z, qa.w + bt * ra.w);
+          rb = make_float4(qb.x + bt * rb.x, qb.y + bt * rb.y, qb.z + bt * rb.z, qb.w + bt * rb.w);
+        } else {
+          ra = mk(qa.x + bt * ra.x, qa.y + bt * ra.y);
+          rb = mk(qb.x + bt * rb.x, qb.y + bt * rb.y);
+        }
+        reinterpret_cast<V*>(const_cast<C*>(ua))[v] = ra;
+        reinterpret_cast<V*>(const_cast<C*>(ub))[v] = rb;
+      }
+#pragma unroll
+      for (int h = 0; h < EPV; ++h) {
+        const int e = e0 + v * EPV + h;
+        C va, vb;
+        if constexpr (EPV == 2) {
+          va = h == 0 ? mk(ra.x, ra.y) : mk(ra.z, ra.w);
+          vb = h == 0 ? mk(rb.x, rb.y) : mk(rb.z, rb.w);
+        } else {
+          va = ra;
+          vb = rb;
+        }
+        const int i1 = e % NX, i2 = e / NX;
+        Basis<R> B;
+        voxel_basis<R>(basis, n, (long long)i3 * NE + e, lam[i1], lam[NX + i2], a3, alpha, beta, B);
+        C o[3];
+        if (grp == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) o[k] = csub(cmul(B.x[k], vb), cmul(B.c[k], va));
+        } else {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) o[k] = cadd(cmulc(B.x[k], va), cmulc(B.c[k], vb));
+        }
+        const int sidx = i2 * PITCH + i1;
+        plane[sidx] = pick3<R>(rank, o[0], o[1], o[2]);
+        plane[sb1 + (e - e0)] = pick3<R>(r1, o[0], o[1], o[2]);
+        plane[sb2 + (e - e0)] = pick3<R>(r2, o[0], o[1], o[2]);
+      }
+    }
+  }
+#else
   V ra[PER], rb[PER];
 #pragma unroll
   for (int b = 0; b < PER; ++b) {
@@ -315,6 +381,7 @@ k_pass1_assemble_ifft_xy(const cplx<R>* u, cplx<R>* __restrict__ fld,
       }
     }
   }
+#endif
   cl.sync();  // staging complete in every CTA of the cluster
   {
     // load this rank's component of the two other thirds from the partners'
