@@ -81,3 +81,32 @@ def test_dense_and_clustered(sym_eig):
     lam = np.repeat([1.0, 2.0, 2.0 + 1e-13, 5.0, -3.0], 6)
     check(sym_eig, Q @ np.diag(lam) @ Q.T)
     check(sym_eig, np.zeros((5, 5)))
+
+
+def test_locked_block_with_coinciding_tridiagonal(sym_eig):
+    """The projected matrix of a deflation check: the locked Ritz values on
+    the diagonal (repeated, as in a degenerate cluster), decoupled from a
+    Lanczos tridiagonal whose eigenvalues include the locked ones (the copies
+    the check is looking for)."""
+    rng = np.random.default_rng(3)
+    lam = np.concatenate([[0.7767] * 3, [0.6957] * 3, 0.4 * rng.random(200)])
+    n = lam.size
+    for steps in (5, 20, 60):
+        v = rng.standard_normal(n)
+        V = [v / np.linalg.norm(v)]
+        a, b = [], []
+        for j in range(steps):
+            w = lam * V[-1]
+            for _ in range(2):
+                for u in V:
+                    w -= (u @ w) * u
+            a.append(V[-1] @ (lam * V[-1]))
+            if j < steps - 1:
+                b.append(np.linalg.norm(w))
+                V.append(w / b[-1])
+        T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+        k = 8
+        A = np.zeros((k + steps, k + steps))
+        A[np.arange(k), np.arange(k)] = [0.7767] * 4 + [0.6957] * 4
+        A[k:, k:] = T
+        check(sym_eig, A)
