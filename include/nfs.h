@@ -194,7 +194,11 @@ int nfs_cg_solve(nfs_ctx* ctx, const void* b, void* x, nfs_solve_info* info);
  * nev largest theta = 1/omega of B_r y = theta A_r y.  The basis is FP64 and
  * A_r-orthogonal: FP64 three-term recurrence, and every step the inner
  * products with all older vectors in double-single arithmetic, removing them
- * when they exceed opt.orth_tol.  omega: HOST array of nev doubles, ascending.
+ * when they exceed opt.orth_tol.  A single start vector finds one copy of an
+ * exactly degenerate eigenvalue (symmetric media and k-points); with
+ * opt.deflation_checks > 0 the converged pairs are locked and the search
+ * restarted from a random vector A_r-orthogonal to them, which brings in the
+ * missing copies.  omega: HOST array of nev doubles, ascending.
  * Y: device complex128 array [nev][4n] of A_r-normalised eigenvectors y, or
  * NULL.  info may be NULL.  Returns NFS_ENOCONV (results still written) if the
  * restart cap is hit first. */
