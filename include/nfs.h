@@ -291,7 +291,9 @@ typedef struct {
  *   omega: HOST, 2 nev doubles (re, im), nearest sigma first.
  *   Y:     DEVICE complex128 [nev][4n] unit eigenvectors y of M, or NULL.
  * Synchronises opt.stream; allocates the Arnoldi and GMRES bases on first
- * use.  Returns NFS_ENOCONV (results written) if the restart cap is hit. */
+ * use.  Returns NFS_ENOCONV with the results written if the restart cap is
+ * hit, and NFS_ENOCONV with nothing written (info->status too) if an inner
+ * GMRES solve reaches opt.cg_maxit products. */
 int nfs_nfsep_eigs(nfs_ctx* ctx, int nev, const double sigma[2], double* omega, void* Y, nfs_nfsep_info* info);
 
 /* Fields of NFSEP eigenvectors (Algorithm 1, second branch): y <- S y, then

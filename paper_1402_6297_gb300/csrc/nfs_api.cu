@@ -1861,7 +1861,18 @@ extern "C" int nfs_nfsep_eigs(nfs_ctx* c, int nev, const double sigma[2], double
   DevShiftInvert op(c, c->zv, c->p64, g, gm, c->opt.cg_tol, c->opt.cg_maxit);
   nfs::host::ArnoldiResult r;
   const int rc = nfs::host::krylov_schur(op, nev, m, c->opt.eig_tol, c->opt.max_restarts, r);
-  if (rc != NFS_OK) return rc;
+  if (rc != NFS_OK) {
+    // an inner solve failed (or a breakdown): nothing to return but the counts
+    if (info) {
+      *info = nfs_nfsep_info{};
+      info->arnoldi_steps = r.steps;
+      info->restarts = r.restarts;
+      info->gmres_iterations = op.inner;
+      info->status = rc;
+      info->kernel_launches = c->launches - launches_0;
+    }
+    return rc;
+  }
   for (int e = 0; e < nev; ++e) {
     const cplxd lam = cplxd(sigma[0], sigma[1]) + 1.0 / r.theta[e];
     omega[2 * e] = lam.real();

@@ -489,7 +489,10 @@ class NFSEPContext:
 
     def eigs(self, nev, sigma, vectors=True, allow_noconv=False):
         """The nev eigenvalues of M nearest the complex shift sigma: (omega
-        complex (nev,), Y (nev, 4n) or None, NfsepInfo)."""
+        complex (nev,), Y (nev, 4n) or None, NfsepInfo).  With allow_noconv an
+        NFS_ENOCONV return is passed through: omega holds the results if the
+        restart cap was hit, zeros if an inner GMRES solve did not converge
+        (info.nconv = 0 then)."""
         torch = self._torch
         sg = np.array([complex(sigma).real, complex(sigma).imag], dtype=np.float64)
         om = np.zeros(2 * nev, dtype=np.float64)
