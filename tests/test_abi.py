@@ -240,3 +240,29 @@ def test_new_entry_points_validate_on_the_host(nfs):
         nfs._material(wl.biisotropic_sphere(g, 0.25, 13.0 + 1j, 1.0, 0.5, 0.0))
     with pytest.raises(ValueError):
         nfs.NFSEPContext(g, (0.1, 0.2, 0.3), med)
+
+
+def test_non_finite_inputs_are_refused(nfs):
+    """Fault injection on the host: NaN or infinite material values and Bloch
+    vectors are rejected by the set-up before any device memory is taken."""
+    g = (8, 8, 8)
+    med = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+    for field, value, code in (("eps", np.nan, nfs.NFS_ENOTHPD), ("eps", np.inf, nfs.NFS_ENOTHPD),
+                               ("gamma", np.nan, nfs.NFS_EINVAL), ("gamma", np.inf, nfs.NFS_EINVAL)):
+        bad = wl.chiral_sphere(g, 0.25, 13.0, 1.0, 0.5)
+        getattr(bad, field)[1, 2, 3, 4] = value
+        assert _setup(nfs, g, (0.1, 0.2, 0.3), bad) == code, (field, value)
+    assert _setup(nfs, g, (0.1, np.nan, 0.3), med) == nfs.NFS_EINVAL
+    assert _setup(nfs, g, (np.inf, 0.2, 0.3), med) == nfs.NFS_EINVAL
+    # bi-isotropic: a NaN anywhere makes B's determinant non-finite
+    L = nfs.lib()
+    sph = wl.biisotropic_sphere(g, 0.25, 13.0 + 2.0j, 1.0, 0.5, 0.2)
+    sph.eps[0, 0, 0, 0] = complex(np.nan, 0.0)
+    arrs = [np.ascontiguousarray(a, dtype=np.complex128) for a in (sph.eps, sph.mu, sph.gamma, sph.chi)]
+    bm = nfs.BiisoMaterial()
+    for name, a in zip(("eps", "mu", "gamma", "chi"), arrs):
+        setattr(bm, name, a.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    h = ctypes.c_void_p()
+    gi = (ctypes.c_int * 3)(*g)
+    kv = np.array([0.1, 0.2, 0.3])
+    assert L.nfs_setup_biiso(ctypes.byref(h), gi, None, nfs._dptr(kv), ctypes.byref(bm), None) == nfs.NFS_EINVAL
