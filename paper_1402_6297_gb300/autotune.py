@@ -43,6 +43,7 @@ KNOBS = {
     "NFS_ZTILE_C64": [16, 8],
     "NFS_C64_PAIRS": [0, 1],
     "NFS_PASS1_FUSED_LOAD": [0, 1],
+    "NFS_SPLIT_C64": [0, 1],
 }
 MIN_GAIN = 0.03  # relative improvement a knob change must show to be taken
 

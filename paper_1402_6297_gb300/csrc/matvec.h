@@ -65,6 +65,8 @@ template <typename R> cudaError_t matvec_launch(const MatvecArgs<R>& a);
 template <typename R> cudaError_t matvec_launch_mask(const MatvecArgs<R>& a, int mask);
 // Split launches used by the eigenvector-gradient path: pass 1 only.
 template <typename R> cudaError_t pass1_launch(const MatvecArgs<R>& a);
+// Kernels one plane pass launches for grids n1 x n1 (1 cluster form, 2 five-pass form).
+template <typename R> int plane_pass_kernels(int n1);
 // Number of p^* A p partials a CG product emits per problem (dot_part entries).
 template <typename R> int matvec_dot_partials(int n1, int n2, int n3);
 

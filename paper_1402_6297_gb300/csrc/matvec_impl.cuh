@@ -68,10 +68,16 @@ template <typename R, int NY>
 constexpr size_t split_col_smem() {
   return (size_t)(NY * (kSplitCols + 1) + NY) * sizeof(cplx<R>);
 }
+// NFS_SPLIT_C64 = 1 runs the complex64 product in the five-pass form wherever
+// the tiles divide the plane (smaller CTAs, more warps per SM, two extra trips
+// of the fields through L2); 0 keeps the cluster form wherever planes fit.
+#ifndef NFS_SPLIT_C64
+#define NFS_SPLIT_C64 0
+#endif
 template <typename R, int NX>
 constexpr bool split_fits() {
-  return !plane_fits<R, NX>() && NX % kSplitRows == 0 && NX % kSplitCols == 0 &&
-         split_row_smem<R, NX>() <= kMaxDynSmem;
+  return (!plane_fits<R, NX>() || (NFS_SPLIT_C64 && sizeof(cplx<R>) == 8)) && NX % kSplitRows == 0 &&
+         NX % kSplitCols == 0 && split_row_smem<R, NX>() <= kMaxDynSmem;
 }
 
 #define NFS_FOR_EACH_SIZE(M) M(8) M(12) M(16) M(24) M(32) M(48) M(64) M(96) M(128)
@@ -266,12 +272,20 @@ int matvec_dot_partials(int n1, int n2, int n3) {
   return split_rt<R>(n1) ? (n2 / kSplitRows) * 2 * n3 : (n1 * n2) / z_tile(n3, (int)sizeof(cplx<R>));
 }
 
+// Kernels one plane pass (1 or 3) launches: 1 in the cluster form, 2 in the
+// five-pass form.
+template <typename R>
+int plane_pass_kernels(int n1) {
+  return split_rt<R>(n1) ? 2 : 1;
+}
+
 #define NFS_INSTANTIATE_MATVEC(R)                                            \
   template bool matvec_supported<R>(int, int, int);                        \
   template cudaError_t matvec_prepare<R>(int, int, int);                   \
   template cudaError_t matvec_launch<R>(const MatvecArgs<R>&);             \
   template cudaError_t matvec_launch_mask<R>(const MatvecArgs<R>&, int);   \
   template cudaError_t pass1_launch<R>(const MatvecArgs<R>&);               \
-  template int matvec_dot_partials<R>(int, int, int);
+  template int matvec_dot_partials<R>(int, int, int);                      \
+  template int plane_pass_kernels<R>(int);
 
 }  // namespace nfs

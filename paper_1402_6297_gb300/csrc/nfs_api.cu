@@ -247,7 +247,7 @@ int matvec(nfs_ctx* c, cudaStream_t s, const nfs::cplx<R>* u, nfs::cplx<R>* Au, 
   a.bs.sskip = sskip;
   cudaError_t e = nfs::matvec_launch<R>(a);
   if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
-  c->launches += 3;
+  c->launches += 1 + 2 * nfs::plane_pass_kernels<R>(c->n1);
   if (sizeof(nfs::cplx<R>) == 8) c->mv32 += c->P; else c->mv64 += c->P;
   return NFS_OK;
 }
@@ -405,7 +405,7 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
   const size_t head = offsetof(CGState, part_a);
   for (;;) {
     CK(cudaGraphLaunch(exec, s));
-    c->launches += 4 * kCgChunk;
+    c->launches += (2 + 2 * nfs::plane_pass_kernels<R>(c->n1)) * kCgChunk;
     CK(cudaMemcpy2DAsync(c->st_host, sizeof(CGState), c->st, sizeof(CGState), head, c->P, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     bool all = true;
@@ -1533,6 +1533,7 @@ extern "C" int nfs_eig_grad(nfs_ctx* c, int m, const double* weights, const void
     g.scale = scale; g.d_eps = d_eps; g.d_gamma = d_gamma; g.stream = s;
     e = nfs::grad_launch(g);
     if (e != cudaSuccess) return cuda_fail(e, "grad launch");
+    c->launches += 2 + nfs::plane_pass_kernels<double>(c->n1);  // B_r, pass 1, gradient
   }
   CK(cudaStreamSynchronize(s));
   return NFS_OK;
@@ -1559,7 +1560,7 @@ extern "C" int nfs_eig_fields(nfs_ctx* c, int m, const void* Yv, void* Xv) {
     f.X = X + (long long)j * 6 * n; f.stream = c->stream;
     e = nfs::fields_launch(f);
     if (e != cudaSuccess) return cuda_fail(e, "fields launch");
-    c->launches += 2;
+    c->launches += 1 + nfs::plane_pass_kernels<double>(c->n1);
   }
   return NFS_OK;
 }
@@ -1620,7 +1621,7 @@ int nfsep_apply(nfs_ctx* c, cudaStream_t s, const double2* y, double2* out, cons
   if (e != cudaSuccess) return cuda_fail(e, "nfsep pass 3");
   e = nfs::nfsep_post(c->Ap64, out, c->lam64, c->n1, c->n2, c->n3, v, sigma, s);
   if (e != cudaSuccess) return cuda_fail(e, "nfsep post");
-  c->launches += 5;
+  c->launches += 3 + 2 * nfs::plane_pass_kernels<double>(c->n1);
   return NFS_OK;
 }
 
@@ -1908,7 +1909,7 @@ extern "C" int nfs_nfsep_fields(nfs_ctx* c, int m, const void* Yv, void* Xv) {
     e = nfs::nfsep_fields((const double2*)c->fld, c->binv64, c->tw64[2], c->bloch64, c->n1, c->n2, c->n3,
                           (double2*)Xv + (long long)j * 6 * n, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "nfsep fields");
-    c->launches += 3;
+    c->launches += 2 + nfs::plane_pass_kernels<double>(c->n1);
   }
   return NFS_OK;
 }
