@@ -20,7 +20,8 @@ media"):
   :class:`workloads.Medium`.
 * :mod:`oracle.gep`   -- Section 3: the discrete GEP (eq. (discrete_GEP_EH)) solved
   directly, densely (tier O1) or by sparse shift-invert (tier O2), through the
-  equivalent Hermitian-definite pencil; eigenvalue gradients.
+  equivalent Hermitian-definite pencil; eigenvalue gradients; the
+  Cholesky-scaled Hermitian matrix A of Theorem lem:skew-symm_A (eq. (mtx_A)).
 * :mod:`oracle.nfgep` -- Sections 4.1-4.2: the HHPD-NFGEP (thm:NFSEP_real_ew),
   the factored A_r (eq. (factor_mtx)) applied with FFTs (tier O3), B_r, CG
   (eq. (spd_LS)), an ARPACK invert-Lanczos eigensolve, and the fields

@@ -49,6 +49,34 @@ def gep_residual(grid, kdota, medium, omega, x, a=1.0):
     return float(np.linalg.norm(L @ x - omega * Bx) / (abs(omega) * np.linalg.norm(Bx)))
 
 
+def hsep_matrix(grid, kdota, medium, a=1.0):
+    """The 6n x 6n Hermitian matrix A of eq. (mtx_A) (Theorem
+    lem:skew-symm_A): with mu_d = mu_c mu_c^* and Phi = Phi_c Phi_c^* the
+    Cholesky factors (eq. (Phi_12)),
+
+        A = -i [[-Phi_c^{-1}(xi mu^{-1} C - C^* mu^{-1} zeta) Phi_c^{-*}, -Phi_c^{-1} C^* mu_c^{-*}],
+                [ mu_c^{-1} C Phi_c^{-*},                                   0                    ]],
+
+    whose eigenvalues are those of the GEP (eq. (discrete_GEP_EH)), zeros
+    included.  Dense; for tiny grids only."""
+    C = yee.curl_matrix(grid, kdota, a).toarray()
+    eps, mu, xi, zeta = (om.block_sparse(t).toarray() for t in om.tensors(medium))
+    mu_inv = np.linalg.inv(mu)
+    phi = eps - xi @ mu_inv @ zeta
+    mu_c = np.linalg.cholesky(mu)
+    phi_c = np.linalg.cholesky(phi)
+    phi_c_inv = np.linalg.inv(phi_c)
+    phi_cH_inv = np.linalg.inv(phi_c.conj().T)
+    mu_c_inv = np.linalg.inv(mu_c)
+    mu_cH_inv = np.linalg.inv(mu_c.conj().T)
+    Ch = C.conj().T
+    A11 = -phi_c_inv @ (xi @ mu_inv @ C - Ch @ mu_inv @ zeta) @ phi_cH_inv
+    A12 = -phi_c_inv @ Ch @ mu_cH_inv
+    A21 = mu_c_inv @ C @ phi_cH_inv
+    Z = np.zeros_like(A11)
+    return -1j * np.block([[A11, A12], [A21, Z]])
+
+
 def pencil_matrices(grid, kdota, medium, a=1.0):
     """(K'', B'') of the Hermitian-definite pencil described in the module docstring."""
     C = yee.curl_matrix(grid, kdota, a)

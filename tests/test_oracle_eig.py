@@ -188,3 +188,25 @@ def test_bz_path_avoids_gamma():
     ks = wl.bz_path_midpoints(48)
     assert ks.shape == (48, 3)
     assert np.all(np.any(np.abs(ks - np.round(ks)) > 1e-6, axis=1))
+
+
+def test_hsep_matrix_is_hermitian_with_the_gep_spectrum(case):
+    """Theorem (lem:skew-symm_A): under the Assumption the Cholesky-scaled A
+    of eq. (mtx_A) is Hermitian and has all 6n eigenvalues of the GEP (the 2n
+    zeros included), so the GEP's eigenvalues are real."""
+    _, med, w, _, _ = case
+    A = gep.hsep_matrix(GRID, K, med)
+    assert np.abs(A - A.conj().T).max() < 1e-12 * np.abs(A).max()
+    lam = np.linalg.eigvalsh(A)
+    assert np.abs(np.sort(lam) - np.sort(w)).max() < 1e-9 * np.abs(w).max()
+
+
+def test_hsep_matrix_with_mu():
+    g = GRID
+    med = wl.chiral_sphere(g, 0.3, 13.0, 1.0, 0.5)
+    rng = np.random.default_rng(11)
+    med = wl.Medium(g, med.kind, med.eps, med.gamma, 1.0 + rng.random(med.eps.shape), med.axes)
+    A = gep.hsep_matrix(g, K, med)
+    assert np.abs(A - A.conj().T).max() < 1e-12 * np.abs(A).max()
+    w, _, _ = gep.dense_eigs(g, K, med)
+    assert np.abs(np.sort(np.linalg.eigvalsh(A)) - np.sort(w)).max() < 1e-9 * np.abs(w).max()
