@@ -138,3 +138,18 @@ def test_both_branches_of_algorithm_1_give_the_same_fields():
         assert cos > 1 - 1e-9
         checked += 1
     assert checked >= 4
+
+
+def test_invariant_subspace_identity(case):
+    """Theorem (thm:nonzero_invariant_subsp), eq. (pf_invariant_1): with
+    W = B^{-1} diag(P_r Sigma^{1/2}, Q_r Sigma^{1/2}) (6n x 4n, the NFSEP's
+    field map applied to the unit vectors), diag(C, C^*) W = B W M: the span
+    of W is invariant under the GEP and M is the GEP restricted to it."""
+    _, med, nf, _, _ = case
+    N = 4 * nf.n
+    W = np.stack([nf.fields(np.eye(N)[:, j]).ravel() for j in range(N)], axis=1)
+    L, B = gep.gep_matrices(GRID, K, med)
+    M = nf.dense()
+    lhs = L @ W
+    rhs = B @ (W @ M)
+    assert np.abs(lhs - rhs).max() < 1e-10 * np.abs(lhs).max()
