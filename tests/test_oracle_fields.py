@@ -82,3 +82,30 @@ def test_gep_residual_closed_form(case):
         assert abs(r - d / (1 + d)) < 1e-9 * d
     # scale-free in x
     assert abs(gep.gep_residual(GRID, K, med, omega[0] * 1.25, (2 - 3j) * x) - 0.2) < 1e-10
+
+
+def test_block_factorisation_of_B_inverse(case):
+    """Eq. (B_inv): B^{-1} = -i [[I, 0], [-mu^{-1} zeta, I]] [[-Phi^{-1} xi mu^{-1},
+    -Phi^{-1}], [mu^{-1}, 0]] (the form the device fields kernel uses through
+    B^{-1}[p; q] = [i w; -i f]) equals the inverse of B (eq. mtx_B) computed
+    by LAPACK."""
+    _, med, nf, _, _ = case
+    from oracle import media as om
+    eps, mu, xi, zeta = (om.block_sparse(t).toarray() for t in om.tensors(med))
+    L, B = gep.gep_matrices(GRID, K, med)
+    n3 = eps.shape[0]
+    I = np.eye(n3)
+    Z = np.zeros_like(I)
+    mu_inv = np.linalg.inv(mu)
+    phi_inv = np.linalg.inv(eps - xi @ mu_inv @ zeta)
+    Binv = -1j * np.block([[I, Z], [-mu_inv @ zeta, I]]) @ np.block([[-phi_inv @ xi @ mu_inv, -phi_inv],
+                                                                     [mu_inv, Z]])
+    ref = np.linalg.inv(B.toarray())
+    assert np.abs(Binv - ref).max() < 1e-12 * np.abs(ref).max()
+    # and the fields route: B^{-1}[p; q] = [i w; -i f] with (f, w) the middle factors of A_r
+    y = wl.random_complex(4 * nf.n, 9)
+    p, q = nf.fields(y)
+    f, w = nf.middle(p, q)
+    x = nf.eigvec_fields(y)
+    assert np.abs(x[:3] - 1j * w).max() < 1e-12 * np.abs(x).max()
+    assert np.abs(x[3:] + 1j * f).max() < 1e-12 * np.abs(x).max()
