@@ -132,6 +132,14 @@ double now_s() {
 
 thread_local char g_errbuf[256];
 
+// Opt-in trace of the Lanczos steps on stderr (NFS_TRACE_LANCZOS set in the
+// environment): per step alpha, beta^2 before and after the
+// re-orthogonalisation, the measured loss and the CG status; read once.
+bool trace_lanczos() {
+  static const bool on = std::getenv("NFS_TRACE_LANCZOS") != nullptr;
+  return on;
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
   std::snprintf(g_errbuf, sizeof(g_errbuf), "%s: %s", what, cudaGetErrorString(e));
   return NFS_ECUDA;
@@ -778,7 +786,12 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       c->sec_solve += now_s() - ts;
       for (int p = 0; p < P; ++p) {
         if (!active[p]) continue;
-        if (so.status[p] == NFS_EBREAKDOWN) return NFS_EBREAKDOWN;
+        if (so.status[p] == NFS_EBREAKDOWN) {
+          if (trace_lanczos())
+            std::fprintf(stderr, "nfs lanczos: problem %d step %d (j %d): CG breakdown after %d iterations, "
+                         "relres %.3e\n", p, steps[p] + 1, j, so.iters[p], so.relres[p]);
+          return NFS_EBREAKDOWN;
+        }
         cg_total[p] += so.iters[p];
         ++steps[p];
       }
@@ -791,6 +804,8 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       std::vector<double> alpha(P);
       for (int p = 0; p < P; ++p) alpha[p] = coef[(size_t)p * 2 * nl + 2 * (j - local_lo)];
       TRY(dots_re(c, s, w, Mw, bb));
+      const std::vector<double> bb_recur = bb;
+      std::vector<double> loss_first(P, 0.0);
       const double tr1 = now_s();
       c->sec_recur += tr1 - tr0;
       // Partial re-orthogonalisation: every step, measure the loss of
@@ -812,6 +827,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
             for (int i = 0; i < local_lo; ++i)
               loss = std::max(loss, std::hypot(d[(size_t)p * 2 * local_lo + 2 * i], d[(size_t)p * 2 * local_lo + 2 * i + 1]));
             loss /= std::sqrt(std::max(bb[p], 1e-300));
+            if (pass == 0) loss_first[p] = loss;
             reorth[p] = pass == 0 ? loss > c->opt.orth_tol : loss > 1e-3 * c->opt.orth_tol + 1e-13;
             any_re = any_re || reorth[p];
             big = big || (reorth[p] && loss > 1e-3);
@@ -828,6 +844,12 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
         }
       }
       c->sec_orth += now_s() - tr1;
+      if (trace_lanczos())
+        for (int p = 0; p < P; ++p)
+          if (active[p])
+            std::fprintf(stderr, "nfs lanczos: problem %d step %d (j %d, lo %d): alpha %.17e beta2 %.6e -> %.6e "
+                         "loss %.3e cg %d relres %.3e\n", p, steps[p], j, local_lo, alpha[p], bb_recur[p], bb[p],
+                         loss_first[p], so.iters[p], so.relres[p]);
       for (int p = 0; p < P; ++p) {
         if (!active[p]) continue;
         if (!(bb[p] > 0)) return NFS_EBREAKDOWN;
