@@ -142,3 +142,22 @@ def test_krylov_schur_leaves_an_invariant_subspace(kl):
     ev = np.linalg.eigvals(A)
     ref = ev[np.argsort(-np.abs(ev))[:nev]]
     assert match(thc, ref) < 1e-10
+
+
+def test_gmres_reports_non_convergence(kl):
+    """A product cap below what the system needs ends GMRES with NFS_ENOCONV
+    (-6) and the residual reached so far."""
+    rng = np.random.default_rng(6)
+    N = 120
+    A = (rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))) / np.sqrt(N) + 1.5 * np.eye(N)
+    b = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    Ac, Ap = cp(A)
+    bc, bp = cp(b)
+    x = np.zeros(N, complex)
+    xc, xp = cp(x)
+    its, rel = ctypes.c_int(), ctypes.c_double()
+    rc = kl.shim_gmres(N, Ap, 0.0, 0.0, bp, xp, 5, 1e-14, 10, ctypes.byref(its), ctypes.byref(rel))
+    assert rc == -6
+    assert its.value == 10
+    assert 1e-14 < rel.value < 1.0
+    assert abs(np.linalg.norm(b - A @ xc) / np.linalg.norm(b) - rel.value) < 1e-12
