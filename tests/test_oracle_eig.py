@@ -228,3 +228,19 @@ def test_gamma_sweep_conditioning():
     assert all(b > a for a, b in zip(conds, conds[1:])), conds
     assert all(b > a for a, b in zip(its, its[1:])), its
     assert conds[-1] > 10 * conds[0]
+
+
+def test_bloch_periodicity_and_reciprocity(case):
+    """Bloch periodicity: the phase exp(i 2 pi k.a_l) (eq. quasi_periodic)
+    depends on k.a_l modulo 1, so shifting one component by an integer leaves
+    the spectrum unchanged.  Reciprocity: chiral and pseudochiral media with
+    xi^* = zeta and real parameters are reciprocal and lossless, so the
+    spectrum at -k equals the one at k."""
+    _, med, w, _, _ = case
+    scale = np.abs(w).max()
+    for shift in ((1.0, 0.0, 0.0), (0.0, -2.0, 1.0)):
+        ks = tuple(a + b for a, b in zip(K, shift))
+        w2, _, _ = gep.dense_eigs(GRID, ks, med)
+        assert np.abs(np.sort(w2) - np.sort(w)).max() < 1e-10 * scale
+    wneg, _, _ = gep.dense_eigs(GRID, tuple(-a for a in K), med)
+    assert np.abs(np.sort(wneg) - np.sort(w)).max() < 1e-10 * scale

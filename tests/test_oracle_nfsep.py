@@ -153,3 +153,17 @@ def test_invariant_subspace_identity(case):
     lhs = L @ W
     rhs = B @ (W @ M)
     assert np.abs(lhs - rhs).max() < 1e-10 * np.abs(lhs).max()
+
+
+def test_tellegen_coupling_breaks_reciprocity():
+    """A Tellegen parameter (chi != 0) makes the medium non-reciprocal: the
+    spectra at k and -k differ; with chi = 0 (the chiral medium) they agree,
+    as the reciprocity pin of the Hermitian branch requires."""
+    kneg = tuple(-x for x in K)
+    tel = wl.biisotropic_sphere(GRID, 0.3, 6.0, 1.0, 0.8, 0.9, mu_in=1.5)
+    chi0 = wl.biisotropic_sphere(GRID, 0.3, 6.0, 1.0, 0.8, 0.0)
+
+    def spectrum(k, med):
+        return np.sort(np.linalg.eigvals(nfsep.NFSEP(GRID, k, med).dense()).real)
+    assert np.abs(spectrum(K, tel) - spectrum(kneg, tel)).max() > 1e-2
+    assert np.abs(spectrum(K, chi0) - spectrum(kneg, chi0)).max() < 1e-10 * np.abs(spectrum(K, chi0)).max()
