@@ -143,7 +143,7 @@ typedef struct {
 
 /* Defaults: FP64, alpha = 2, beta = 3, cg_tol 1e-12, cg_maxit 2000,
  * inner_tol 1e-6, max_refine 8, eig_tol 1e-10, ncv 0, max_restarts 200,
- * orth_tol 1e-10, seed 1, default stream. */
+ * orth_tol 1e-10, deflation_checks 0, seed 1, default stream. */
 void nfs_default_options(nfs_options* opt);
 
 /* Build a context for one Bloch problem (Algorithm alg:NullSpaceFree, steps
