@@ -85,6 +85,8 @@ def test_default_options(nfs):
     assert o.precision == nfs.PREC_FP64
     assert (o.alpha, o.beta) == (2.0, 3.0)
     assert o.cg_tol == 1e-12 and o.eig_tol == 1e-10
+    assert o.cg_maxit == 2000 and o.max_restarts == 200 and o.orth_tol == 1e-10
+    assert o.deflation_checks == 0 and o.seed == 1 and o.ncv == 0
     assert nfs.lib().nfs_strerror(nfs.NFS_EKPOINT).decode().startswith("k.a_l")
 
 
