@@ -37,6 +37,10 @@ class NFGEP:
         eps, mu, xi, zeta = om.tensors(medium)
         self.mu_inv = om.batched_inv(mu)
         self.xi, self.zeta = xi, zeta
+        # the fixed per-voxel factors xi mu^{-1} and mu^{-1} zeta of eq.
+        # (factor_mtx), formed once per medium rather than in every product
+        self.xi_mu_inv = om.tmul(xi, self.mu_inv)
+        self.mu_inv_zeta = om.tmul(self.mu_inv, zeta)
         # Phi = eps_d - xi_d mu_d^{-1} zeta_d (Section 4.1)
         self.phi_inv = om.batched_inv(eps - om.tmul(om.tmul(xi, self.mu_inv), zeta))
         n1, n2, n3 = grid
@@ -53,13 +57,13 @@ class NFGEP:
         """Apply the three middle factors of A_r to the real-space pair (p, q);
         returns (f, w), the inputs of P_r^* and Q_r^*."""
         # [[xi mu^{-1}, I], [-I, 0]] [p; q]
-        a = om.tapply(om.tmul(self.xi, self.mu_inv), p) + q
+        a = om.tapply(self.xi_mu_inv, p) + q
         b = -p
         # diag(Phi^{-1}, mu^{-1})
         c = om.tapply(self.phi_inv, a)
         d = om.tapply(self.mu_inv, b)
         # [[mu^{-1} zeta, -I], [I, 0]]
-        f = om.tapply(om.tmul(self.mu_inv, self.zeta), c) - d
+        f = om.tapply(self.mu_inv_zeta, c) - d
         w = c
         return f, w
 
