@@ -1,6 +1,9 @@
 """Writes the stored expected values under tests/golden/ from the oracle alone.
 
 Run from the repository root:  python tests/golden/make_golden.py
+The large tier-O3 solves of the benchmark workloads take from an hour to
+several hours of CPU time each and run only when named:
+    python tests/golden/make_golden.py sphere64 pseudo96
 
 Every file records the workload, the oracle tier that produced it and the
 paper's passage that defines the quantity.
@@ -8,6 +11,7 @@ paper's passage that defines the quantity.
 
 import os
 import sys
+import time
 
 import numpy as np
 
@@ -93,5 +97,34 @@ oracle tier O1: dense Hermitian-definite pencil (oracle.gep.dense_eigs), FP64
             f.write(f"{w.real:.17e} {w.imag:.17e}\n")
 
 
+def large(name):
+    """The 20 smallest positive eigenvalues of a benchmark workload by the
+    FFT NFGEP (tier O3: ARPACK invert Lanczos with CG solves at tolerance
+    1e-13), with the wall time and the number of A_r products recorded."""
+    w = wl.workload(name)
+    O = nfgep.NFGEP(w["grid"], w["kdota"], w["medium"])
+    t0 = time.time()
+    om, _ = O.eigs(w["nev"], tol=1e-12, cg_tol=1e-13)
+    dt = time.time() - t0
+    g = w["grid"]
+    desc = {
+        "sphere64": "chiral sphere centred in the cell, radius U[0.2, 0.3] and gamma U[0.3, 0.8] drawn with seed 0,\n"
+                    "eps 13 inside, 1 outside, mu = 1",
+        "pseudo96": "4 z-cylinders radius 0.1 with seeded centres (seed 0), eps 13 inside, 1 outside,\n"
+                    "pseudochiral x-y coupling (eq. (pseudo_chiral_para_mtx)) gamma = 0.4 everywhere, mu = 1",
+    }[name]
+    write(f"{name}_omega.txt", f"""
+{w["nev"]} smallest positive eigenvalues omega of the discrete GEP (Sec. 3, eq. (discrete_GEP_EH)),
+ascending; workload {name}: grid {g[0]}x{g[1]}x{g[2]}, a = 1, k.a = {tuple(w["kdota"])},
+{desc}
+oracle tier O3: FFT NFGEP (oracle.nfgep.NFGEP.eigs: ARPACK invert Lanczos, ncv {max(3 * w["nev"], 2 * w["nev"] + 1)},
+tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s on one host core
+""", om)
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1:
+        for name in sys.argv[1:]:
+            large(name)
+    else:
+        main()
