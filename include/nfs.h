@@ -320,7 +320,7 @@ int nfs_nfsep_fields(nfs_ctx* ctx, int m, const void* Y, void* X);
  *   alpha, beta       basis parameters (eq. mtx_Lambda_p_q), e.g. 2 and 3
  *   u, Au             DEVICE complex128, 4n each, not overlapping
  *   stream            cudaStream_t (NULL = default stream)
- * Workspace: one fixed device array of about 4.8 MB inside the library,
+ * Workspace: one fixed device array of 4,731,136 bytes (4.5 MiB) inside the library,
  * created when the library's device code is loaded and held by every GPU
  * that loads it until the process exits.  The first call on a device looks up
  * that array's device address and sets the kernels' shared-memory limits;
@@ -328,8 +328,9 @@ int nfs_nfsep_fields(nfs_ctx* ctx, int m, const void* Y, void* X);
  * array, so calls that overlap on the GPU (two streams, two host threads)
  * race and must be serialised by the caller.  The call is synchronous with
  * respect to `stream`: it returns after Au is written.  Returns NFS_ENOTHPD if
- * Phi = eps - gamma^2 <= 0 at some voxel (Au is then meaningless), and the
- * Lemma's NFS_EKPOINT / NFS_EBASIS like nfs_setup. */
+ * Phi = eps - gamma^2 <= 0 at some voxel and NFS_EINVAL if an eps or gamma is
+ * not finite (Au is then meaningless; the next call starts from a cleared
+ * status), and the Lemma's NFS_EKPOINT / NFS_EBASIS like nfs_setup. */
 int nfs_matvec_noalloc(const int grid[3], const double k[3], int kind, int axis_a, int axis_b,
                        const double* eps, const double* gamma, double alpha, double beta,
                        const void* u, void* Au, void* stream);

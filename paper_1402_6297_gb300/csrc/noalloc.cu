@@ -33,7 +33,7 @@ constexpr int kMaxDevices = 64;
 //   gamma    3 n double             (chiral: per component; pseudochiral: first n)
 //   lambda   3 * kMaxEdge complex128 (Lambda_1 | Lambda_2 | Lambda_3)
 //   twiddle  3 * kMaxEdge complex128 (exp(-2 pi i m / n_l) per axis)
-//   status   int                    (set when Phi <= 0 somewhere)
+//   status   int                    (1: Phi <= 0 somewhere; 2: eps or gamma not finite)
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffFld = 0;
 constexpr size_t kOffPhi = align256(kOffFld + 6 * kMaxVoxels * sizeof(double2));
@@ -42,6 +42,7 @@ constexpr size_t kOffLam = align256(kOffGam + 3 * kMaxVoxels * sizeof(double));
 constexpr size_t kOffTw = align256(kOffLam + 3 * kMaxEdge * sizeof(double2));
 constexpr size_t kOffStatus = align256(kOffTw + 3 * kMaxEdge * sizeof(double2));
 constexpr size_t kScratchBytes = align256(kOffStatus + sizeof(int));
+static_assert(kScratchBytes == 4731136, "the workspace size documented in nfs.h");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -92,7 +93,13 @@ __global__ void k_noalloc_prep(Tables t, const double* __restrict__ eps, const d
         phi = (c == ax_a || c == ax_b) ? e - g * g : e;
         if (c == 0) t.gam[v] = g;
       }
-      if (!(phi > 0.0)) atomicExch(t.status, 1);
+      // a non-finite eps or gamma is a bad argument (NFS_EINVAL, as nfs_setup
+      // returns); otherwise Phi must be positive (NFS_ENOTHPD)
+      if (!isfinite(e) || !isfinite(g)) {
+        atomicMax(t.status, 2);
+      } else if (!(phi > 0.0)) {
+        atomicMax(t.status, 1);
+      }
       t.inv_phi[c * n + v] = 1.0 / phi;
     }
   }
@@ -211,5 +218,5 @@ extern "C" int nfs_matvec_noalloc(const int grid[3], const double k[3], int kind
   if (e != cudaSuccess) return NFS_ECUDA;
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return NFS_ECUDA;
-  return status ? NFS_ENOTHPD : NFS_OK;
+  return status == 2 ? NFS_EINVAL : (status ? NFS_ENOTHPD : NFS_OK);
 }

@@ -50,3 +50,41 @@ def test_noalloc_rejects_grids_beyond_its_workspace(lib):
     with pytest.raises(lib.NFSError) as exc:
         lib.matvec_noalloc(g, K, "chiral", (0, 1), _device(med.eps), _device(med.gamma), u, torch.empty_like(u))
     assert exc.value.code == lib.NFS_EUNSUPPORTED
+
+
+def test_noalloc_status_word_is_cleared_between_calls(lib):
+    # Phi = eps - gamma^2 < 0 at one voxel: NFS_ENOTHPD.  The next valid call
+    # must start from a cleared status word and match the context product.
+    g = (16, 16, 24)
+    med = wl.chiral_sphere(g, 0.3, 13.0, 1.0, 0.6)
+    u = _device(wl.random_complex(4 * 16 * 16 * 24, 4))
+    out = torch.empty_like(u)
+    bad_eps = med.eps.copy()
+    assert med.gamma[1, 12, 8, 8] == 0.6  # inside the sphere
+    bad_eps[1, 12, 8, 8] = 0.5 * med.gamma[1, 12, 8, 8] ** 2
+    with pytest.raises(lib.NFSError) as exc:
+        lib.matvec_noalloc(g, K, "chiral", (0, 1), _device(bad_eps), _device(med.gamma), u, out)
+    assert exc.value.code == lib.NFS_ENOTHPD
+    # a non-finite permittivity is a bad argument, as for nfs_setup
+    inf_eps = med.eps.copy()
+    inf_eps[0, 0, 0, 0] = np.inf
+    with pytest.raises(lib.NFSError) as exc:
+        lib.matvec_noalloc(g, K, "chiral", (0, 1), _device(inf_eps), _device(med.gamma), u, out)
+    assert exc.value.code == lib.NFS_EINVAL
+    ctx = lib.Context(g, K, med)
+    ref = ctx.matvec(u)
+    ctx.close()
+    lib.matvec_noalloc(g, K, "chiral", (0, 1), _device(med.eps), _device(med.gamma), u, out)
+    err = ((out - ref).abs().max() / ref.abs().max()).item()
+    assert err < 1e-12, err
+
+
+def test_noalloc_rejects_the_gamma_point(lib):
+    # k.a_l all integers: Lambda_q vanishes at one voxel (the Lemma)
+    g = (16, 16, 16)
+    med = wl.chiral_sphere(g)
+    u = torch.zeros(4 * 16 ** 3, dtype=torch.complex128, device="cuda")
+    with pytest.raises(lib.NFSError) as exc:
+        lib.matvec_noalloc(g, (0.0, 0.0, 0.0), "chiral", (0, 1), _device(med.eps), _device(med.gamma), u,
+                           torch.empty_like(u))
+    assert exc.value.code == lib.NFS_EKPOINT
