@@ -23,6 +23,20 @@ struct BatchStrides {
   int sskip = 0;         // skip
 };
 
+struct CGState;
+
+// CG step fused into pass 3 (cluster form): instead of writing A_r p, pass 3
+// forms x += alpha p and r -= alpha A_r p per voxel with alpha = rr / p^*A p
+// (from pass 2's partials), and its last CTA the new r^* r, beta and the
+// convergence state (the separate x/r update kernel is then not launched).
+template <typename R>
+struct CgFuse {
+  cplx<R>* x = nullptr;
+  cplx<R>* r = nullptr;
+  const cplx<R>* p = nullptr;
+  CGState* st = nullptr;  // per problem: st + prob
+};
+
 template <typename R>
 struct MatvecArgs {
   const cplx<R>* u;       // 4n, spectral
@@ -44,9 +58,12 @@ struct MatvecArgs {
   const cplx<R>* basis;
   cudaStream_t stream;
   // CG fusion (both optional, nullptr when unused):
-  const cplx<R>* cg_r;    // pass 1 first forms u = cg_r + (*cg_beta) u in place
+  const cplx<R>* cg_r;    // pass 1 first forms p = cg_r + (*cg_beta) u ...
   const double* cg_beta;
+  cplx<R>* p_out;         // ... and stores it here (nullptr: in place, into u; the
+                          // paired complex64 kernels need a separate buffer)
   double* dot_part;       // one partial of Re(u^* A u) per CTA of pass 2 (pass 3b in the five-pass form)
+  CgFuse<R> cg;           // optional: the CG step fused into pass 3 (see cg_fusable)
   // batching: P problems of this grid in one launch (P = 1 for one problem)
   int P;
   BatchStrides bs;
@@ -67,6 +84,13 @@ template <typename R> cudaError_t matvec_launch_mask(const MatvecArgs<R>& a, int
 template <typename R> cudaError_t pass1_launch(const MatvecArgs<R>& a);
 // Kernels one plane pass launches for grids n1 x n1 (1 cluster form, 2 five-pass form).
 template <typename R> int plane_pass_kernels(int n1);
+// Kernels one whole product launches for grids n1 x n1.
+template <typename R> int product_kernels(int n1);
+// Whether the CG direction update of pass 1 needs p_out distinct from u
+// (the paired complex64 plane kernels read every voxel of u in three CTAs).
+template <typename R> bool cg_needs_p_out(int n1);
+// Whether pass 3 can take the CG step (MatvecArgs::cg) for grids n1 x n1.
+template <typename R> bool cg_fusable(int n1);
 // Number of p^* A p partials a CG product emits per problem (dot_part entries).
 template <typename R> int matvec_dot_partials(int n1, int n2, int n3);
 

@@ -3,6 +3,7 @@
 #pragma once
 #include "matvec.h"
 #include "matvec_kernels.cuh"
+#include "matvec_pk.cuh"
 #include "matvec_split.cuh"
 
 namespace nfs {
@@ -82,9 +83,47 @@ constexpr bool split_fits() {
 
 #define NFS_FOR_EACH_SIZE(M) M(8) M(12) M(16) M(24) M(32) M(48) M(64) M(96) M(128)
 
+// The paired complex64 kernels (matvec_pk.cuh) replace the unpaired ones at
+// the lengths they exist for; NFS_PK = 0 keeps the unpaired kernels everywhere.
+#ifndef NFS_PK
+#define NFS_PK 1
+#endif
+template <typename R, int N>
+constexpr bool use_pk() {
+  return NFS_PK && std::is_same<R, float>::value && pk_plane_used(N) && pk_plane_smem<N>() <= kMaxDynSmem;
+}
+// Pass 3 in the paired form (1) or the unpaired cluster form (0): the paired
+// pass 3 needs its own projection kernel (a CTA holds one component of the
+// pair), which costs more than it saves.
+#ifndef NFS_PK3
+#define NFS_PK3 0
+#endif
+template <typename R, int N>
+constexpr bool use_pk3() {
+  return NFS_PK3 && use_pk<R, N>();
+}
+template <typename R, int N3>
+constexpr bool use_pk_z() {
+  return NFS_PK && std::is_same<R, float>::value && pk_z_used(N3) && pk_z_smem<N3>() <= kMaxDynSmem;
+}
+
 template <typename R, int NX>
 static cudaError_t plane_prepare() {
-  if constexpr (split_fits<R, NX>()) {
+  if constexpr (use_pk<R, NX>()) {
+    constexpr int NT1 = pk_plane_threads(NX, 1), MB1 = pk_plane_minb(NX, 1);
+    constexpr int NT3 = pk_plane_threads(NX, 3), MB3 = pk_plane_minb(NX, 3);
+    cudaError_t e = cudaFuncSetAttribute(k_pk_pass1<NX, NT1, MB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pk_plane_smem<NX>());
+    if (e != cudaSuccess) return e;
+    if constexpr (use_pk3<R, NX>()) {
+      return cudaFuncSetAttribute(k_pk_pass3<NX, NT3, MB3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pk_plane_smem<NX>());
+    } else {
+      constexpr int NT = plane_threads(NX);
+      return cudaFuncSetAttribute(k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem<R, NX>());
+    }
+  } else if constexpr (split_fits<R, NX>()) {
     cudaError_t e = cudaFuncSetAttribute(k_pass1a_assemble_fft_x<R, NX, kSplitRows, kSplitRowThreads>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_row_smem<R, NX>());
     if (e != cudaSuccess) return e;
@@ -111,6 +150,10 @@ static cudaError_t plane_prepare() {
 
 template <typename R, int N3>
 static cudaError_t z_prepare() {
+  if constexpr (use_pk_z<R, N3>()) {
+    return cudaFuncSetAttribute(k_pk_pass2<N3, pk_z_threads(N3), pk_z_minb(N3)>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk_z_smem<N3>());
+  }
   constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
   constexpr int NT = z_threads(N3, (int)sizeof(cplx<R>));
   return cudaFuncSetAttribute(k_pass2_z_material<R, N3, TX, NT, z_minb(N3, (int)sizeof(cplx<R>))>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -119,7 +162,32 @@ static cudaError_t z_prepare() {
 
 template <typename R, int NX>
 static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
-  if constexpr (split_fits<R, NX>()) {
+  if constexpr (use_pk<R, NX>()) {
+    constexpr int NT1 = pk_plane_threads(NX, 1), MB1 = pk_plane_minb(NX, 1);
+    constexpr int NT3 = pk_plane_threads(NX, 3), MB3 = pk_plane_minb(NX, 3);
+    const dim3 grid(3, a.n3 * (a.P > 0 ? a.P : 1));
+    if (which == 1) {
+      if (a.cg_r != nullptr && (a.p_out == nullptr || (const void*)a.p_out == (const void*)a.u))
+        return cudaErrorInvalidValue;  // the direction update needs its own output buffer
+      k_pk_pass1<NX, NT1, MB1><<<grid, NT1, pk_plane_smem<NX>(), a.stream>>>(
+          a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.p_out, a.bs);
+    } else if constexpr (use_pk3<R, NX>()) {
+      if (a.cg.st != nullptr) return cudaErrorInvalidValue;  // no fused CG step in this form
+      k_pk_pass3<NX, NT3, MB3><<<grid, NT3, pk_plane_smem<NX>(), a.stream>>>(a.fld, a.tw1, a.tw2, a.n3, a.skip,
+                                                                             a.bs);
+      constexpr int per_plane = (NX * NX + kProjThreads * kProjV - 1) / (kProjThreads * kProjV);
+      k_pk_project<NX><<<per_plane * a.n3 * (a.P > 0 ? a.P : 1), kProjThreads, 0, a.stream>>>(
+          a.fld, a.Au, a.lam, a.n3, a.alpha, a.beta, a.skip, a.bs);
+    } else {
+      constexpr int NT = plane_threads(NX);
+      dim3 grid3(3, 2, a.n3 * (a.P > 0 ? a.P : 1));
+      k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))>
+          <<<grid3, NT, plane_smem<R, NX>(), a.stream>>>(a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta,
+                                                          a.skip, a.basis, a.bs, a.cg);
+    }
+    return cudaGetLastError();
+  } else if constexpr (split_fits<R, NX>()) {
+    if (a.cg.st != nullptr) return cudaErrorInvalidValue;  // no fused CG step in the five-pass form
     const int P = a.P > 0 ? a.P : 1;
     const dim3 rows(a.n2 / kSplitRows, 2, a.n3 * P), cols(a.n1 / kSplitCols, 6, a.n3 * P);
     if (which == 1) {
@@ -144,7 +212,7 @@ static cudaError_t plane_launch(const MatvecArgs<R>& a, int which) {
           a.u, a.fld, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.cg_r, a.cg_beta, a.basis, a.bs);
     } else {
       k_pass3_fft_xy_project<R, NX, NX, NT, plane_minb(NX, (int)sizeof(cplx<R>))><<<grid, NT, plane_smem<R, NX>(), a.stream>>>(
-          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.basis, a.bs);
+          a.fld, a.Au, a.lam, a.tw1, a.tw2, a.n3, a.alpha, a.beta, a.skip, a.basis, a.bs, a.cg);
     }
     return cudaGetLastError();
   } else {
@@ -157,6 +225,16 @@ static bool split_rt(int n);
 
 template <typename R, int N3>
 static cudaError_t z_launch(const MatvecArgs<R>& a) {
+  if constexpr (use_pk_z<R, N3>()) {
+    static_assert(kPkZTile == z_tile(N3, 8), "one CG curvature partial per CTA of either z pass");
+    const int ncols = a.n1 * a.n2;
+    MatView<float> mv{a.inv_phi, a.gam, a.inv_mu, a.kind, a.ax_a, a.ax_b, (long long)ncols * a.n3};
+    const float inv_n = (float)(1.0 / ((double)ncols * (double)a.n3));
+    k_pk_pass2<N3, pk_z_threads(N3), pk_z_minb(N3)>
+        <<<(ncols / kPkZTile) * (a.P > 0 ? a.P : 1), pk_z_threads(N3), pk_z_smem<N3>(), a.stream>>>(
+            a.fld, mv, a.tw3, ncols, inv_n, a.skip, split_rt<R>(a.n1) ? nullptr : a.dot_part, a.bs);
+    return cudaGetLastError();
+  }
   constexpr int TX = z_tile(N3, (int)sizeof(cplx<R>));
   constexpr int NT = z_threads(N3, (int)sizeof(cplx<R>));
   const int ncols = a.n1 * a.n2;
@@ -272,11 +350,45 @@ int matvec_dot_partials(int n1, int n2, int n3) {
   return split_rt<R>(n1) ? (n2 / kSplitRows) * 2 * n3 : (n1 * n2) / z_tile(n3, (int)sizeof(cplx<R>));
 }
 
+template <typename R>
+bool cg_needs_p_out(int n1) {
+  switch (n1) {
+#define NFS_CASE(N) case N: return use_pk<R, N>();
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return false;
+}
+
 // Kernels one plane pass (1 or 3) launches: 1 in the cluster form, 2 in the
 // five-pass form.
 template <typename R>
 int plane_pass_kernels(int n1) {
   return split_rt<R>(n1) ? 2 : 1;
+}
+
+// Kernels of one whole product: 3 in the cluster form, 5 in the five-pass
+// form, 4 in the paired form (pass 3 and its projection kernel).
+template <typename R>
+bool cg_fusable(int n1) {
+  if (split_rt<R>(n1)) return false;
+  switch (n1) {
+#define NFS_CASE(N) case N: return !use_pk3<R, N>();
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return false;
+}
+
+template <typename R>
+int product_kernels(int n1) {
+  if (split_rt<R>(n1)) return 5;
+  switch (n1) {
+#define NFS_CASE(N) case N: return use_pk3<R, N>() ? 4 : 3;
+    NFS_FOR_EACH_SIZE(NFS_CASE)
+#undef NFS_CASE
+  }
+  return 3;
 }
 
 #define NFS_INSTANTIATE_MATVEC(R)                                            \
@@ -286,6 +398,9 @@ int plane_pass_kernels(int n1) {
   template cudaError_t matvec_launch_mask<R>(const MatvecArgs<R>&, int);   \
   template cudaError_t pass1_launch<R>(const MatvecArgs<R>&);               \
   template int matvec_dot_partials<R>(int, int, int);                      \
-  template int plane_pass_kernels<R>(int);
+  template int plane_pass_kernels<R>(int);                                 \
+  template bool cg_needs_p_out<R>(int);                                    \
+  template int product_kernels<R>(int);                                    \
+  template bool cg_fusable<R>(int);
 
 }  // namespace nfs

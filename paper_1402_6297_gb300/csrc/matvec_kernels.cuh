@@ -38,6 +38,7 @@
 
 #include <type_traits>
 
+#include "cg_state.cuh"
 #include "fft_smem.cuh"
 #include "matvec.h"
 
@@ -561,7 +562,8 @@ __global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(NT, MINB)
 k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au,
                        const cplx<R>* __restrict__ lam, const cplx<R>* __restrict__ twx,
                        const cplx<R>* __restrict__ twy, int n3, R alpha, R beta,
-                       const int* __restrict__ skip, const cplx<R>* __restrict__ basis, BatchStrides bs) {
+                       const int* __restrict__ skip, const cplx<R>* __restrict__ basis, BatchStrides bs,
+                       CgFuse<R> cg) {
   using C = cplx<R>;
   constexpr int PITCH = NX + 1;
   constexpr int NE = NX * NY;
@@ -583,7 +585,29 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   for (int i = threadIdx.x; i < NX; i += NT) stx[i] = twx[i];
   for (int i = threadIdx.x; i < NY; i += NT) sty[i] = twy[i];
   const C* in = fld + ((long long)(grp * 3 + rank) * n3 + i3) * NE;
-  __syncthreads();  // twiddles
+  // fused CG step: alpha from pass 2's partials of p^* A p, summed in the same
+  // fixed order by every CTA (so all agree); no state is written until the
+  // last CTA of the launch (the `done` flag every CTA reads at its start must
+  // not change while the launch runs)
+  __shared__ double s_cg_alpha;
+  __shared__ int s_cg_ok, s_cg_last;
+  // (only complex64 and complex128 run CG; the double-single product never does)
+  constexpr bool CGT = std::is_same<R, float>::value || std::is_same<R, double>::value;
+  CGState* cst = (CGT && cg.st != nullptr) ? cg.st + prob : nullptr;
+  if (cst != nullptr) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < cst->npart_a; i += NT) v += cst->part_a[i];
+    const double pAp = block_sum_dbl<NT>(v);
+    if (threadIdx.x == 0) {
+      s_cg_alpha = cst->rr / pAp;
+      s_cg_ok = (pAp > 0.0) && (s_cg_alpha == s_cg_alpha);  // also catches NaN
+      if (blockIdx.x == 0 && blockIdx.y == 0 && i3 == 0) {
+        cst->pAp = pAp;
+        cst->alpha = s_cg_alpha;
+      }
+    }
+  }
+  __syncthreads();  // twiddles (and alpha)
   // the 2-D DFT along y first (columns, read from global memory straight into
   // registers), then along x
   smem_fft_io<false, NY, NX, NT, 1, PITCH, true, false>(plane, sty,
@@ -601,6 +625,12 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   using V = typename Lane<C>::V;
   V* o0v = reinterpret_cast<V*>(o0);
   V* o1v = reinterpret_cast<V*>(o1);
+  const bool cg_on = cst != nullptr;
+  const bool cg_upd = cg_on && s_cg_ok;
+  const R cg_al = cg_on ? (R)s_cg_alpha : (R)0;
+  const long long cg_off = prob * bs.su + (2 * grp) * n + (long long)i3 * NE;
+  using AccT = typename std::conditional<CGT, C, double2>::type;
+  Acc<AccT> cg_acc;
   // EPV consecutive elements per lane (e0, e1 even)
   for (int ev = e0 / EPV + (int)threadIdx.x; ev < e1 / EPV; ev += NT) {
     C r0[EPV], r1[EPV];
@@ -622,12 +652,71 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
         r1[h] = cadd(cadd(cmul(B.c[0], f[0]), cmul(B.c[1], f[1])), cmul(B.c[2], f[2]));
       }
     }
-    if constexpr (EPV == 2) {
+    if (cg_on) {
+      // x += alpha p, r -= alpha A_r p (this CTA's third of its two quarters)
+      if constexpr (CGT) if (cg_upd) {
+#pragma unroll
+        for (int h = 0; h < EPV; ++h) {
+          const long long i0 = cg_off + ev * EPV + h, i1 = i0 + n;
+          const C pa = cg.p[i0], pb = cg.p[i1];
+          C xa = cg.x[i0], xb = cg.x[i1], ra = cg.r[i0], rb = cg.r[i1];
+          xa = mk(xa.x + cg_al * pa.x, xa.y + cg_al * pa.y);
+          xb = mk(xb.x + cg_al * pb.x, xb.y + cg_al * pb.y);
+          ra = mk(ra.x - cg_al * r0[h].x, ra.y - cg_al * r0[h].y);
+          rb = mk(rb.x - cg_al * r1[h].x, rb.y - cg_al * r1[h].y);
+          cg.x[i0] = xa;
+          cg.x[i1] = xb;
+          cg.r[i0] = ra;
+          cg.r[i1] = rb;
+          cg_acc.add(ra.x * ra.x + ra.y * ra.y + rb.x * rb.x + rb.y * rb.y);
+        }
+      }
+    } else if constexpr (EPV == 2) {
       o0v[ev] = make_float4(r0[0].x, r0[0].y, r0[1].x, r0[1].y);
       o1v[ev] = make_float4(r1[0].x, r1[0].y, r1[1].x, r1[1].y);
     } else {
       o0v[ev] = r0[0];
       o1v[ev] = r1[0];
+    }
+  }
+  if (cg_on) {
+    // this CTA's partial of the new r^* r; the last CTA to arrive (atomic
+    // count, no waiting) sums them in fixed order and sets beta, the
+    // iteration count and the convergence state for the next launch
+    const int ncta = 6 * n3;
+    const int cta = rank + 3 * (grp + 2 * i3);
+    const double part = block_sum_dbl<NT>(cg_acc.total());
+    if (threadIdx.x == 0) {
+      cst->part_b[cta] = part;
+      __threadfence();
+      s_cg_last = atomicAdd(&cst->arrived, 1u) == (unsigned)ncta - 1;
+    }
+    __syncthreads();
+    if (s_cg_last) {
+      __threadfence();
+      double v = 0.0;
+      for (int i = threadIdx.x; i < ncta; i += NT) v += ((volatile double*)cst->part_b)[i];
+      const double rr = block_sum_dbl<NT>(v);
+      if (threadIdx.x == 0) {
+        cst->arrived = 0;
+        if (!s_cg_ok) {
+          cst->status = -7;  // breakdown: x, r left untouched
+          cst->done = 1;
+        } else {
+          cst->it += 1;
+          if (!(rr == rr)) {
+            cst->status = -7;
+            cst->done = 1;
+          } else if (rr <= cst->tol2) {
+            cst->done = 1;
+          } else if (cst->it >= cst->maxit) {
+            cst->status = -6;
+            cst->done = 1;
+          }
+          cst->beta = rr / cst->rr;
+          cst->rr = rr;
+        }
+      }
     }
   }
   cl.sync();  // keep this CTA's plane alive until the cluster finished reading it

@@ -88,6 +88,7 @@ struct nfs_ctx {
   void* fld = nullptr;  // 6n complex128 each (complex64 uses 12n entries of it)
   double2 *x64 = nullptr, *r64 = nullptr, *p64 = nullptr, *Ap64 = nullptr, *t64 = nullptr, *t64b = nullptr;
   float2 *x32 = nullptr, *r32 = nullptr, *p32 = nullptr, *Ap32 = nullptr;
+  float2* p32b = nullptr;  // second CG direction buffer when pass 1 cannot update in place
   CGState* st = nullptr;
   CGState* st_host = nullptr;  // pinned mirror of the scalar part
   // small per-problem arrays (device + pinned host): tolerances, scales, flags
@@ -255,7 +256,7 @@ int matvec(nfs_ctx* c, cudaStream_t s, const nfs::cplx<R>* u, nfs::cplx<R>* Au, 
   a.bs.sskip = sskip;
   cudaError_t e = nfs::matvec_launch<R>(a);
   if (e != cudaSuccess) return cuda_fail(e, "matvec launch");
-  c->launches += 1 + 2 * nfs::plane_pass_kernels<R>(c->n1);
+  c->launches += nfs::product_kernels<R>(c->n1);
   if (sizeof(nfs::cplx<R>) == 8) c->mv32 += c->P; else c->mv64 += c->P;
   return NFS_OK;
 }
@@ -345,12 +346,34 @@ cudaError_t enqueue_cg_chunk(nfs_ctx* c, cudaStream_t s, nfs::cplx<R>* x, nfs::c
   a.cg_r = r;
   a.cg_beta = &c->st->beta;
   a.dot_part = c->st->part_a;
+  // kernels that cannot form p = r + beta p in place alternate between p and
+  // a second buffer (kCgChunk is even: p holds the direction after a chunk)
+  C* p2 = nullptr;
+  if (sizeof(R) == 4 && nfs::cg_needs_p_out<R>(c->n1)) p2 = reinterpret_cast<C*>(c->p32b);
+  static_assert(kCgChunk % 2 == 0, "the direction must end a chunk in p");
+  // where pass 3 can take the x/r step itself, no update kernel runs and A p
+  // is never stored
+  const bool fused = nfs::cg_fusable<R>(c->n1);
   for (int i = 0; i < kCgChunk; ++i) {
+    C* pn = p;
+    if (p2 != nullptr) {
+      a.u = (i % 2 == 0) ? p : p2;
+      pn = (i % 2 == 0) ? p2 : p;
+      a.p_out = pn;
+    }
+    if (fused) {
+      a.cg.x = x;
+      a.cg.r = r;
+      a.cg.p = pn;
+      a.cg.st = c->st;
+    }
     cudaError_t e = nfs::matvec_launch<R>(a);
     if (e != cudaSuccess) return e;
-    nfs::k_cg_update_xr<C><<<dim3(nfs::kUpdBlocks, c->P), nfs::kUpdThreads, 0, s>>>(x, r, p, Ap, c->N, c->st);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (!fused) {
+      nfs::k_cg_update_xr<C><<<dim3(nfs::kUpdBlocks, c->P), nfs::kUpdThreads, 0, s>>>(x, r, pn, Ap, c->N, c->st);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -413,7 +436,7 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
   const size_t head = offsetof(CGState, part_a);
   for (;;) {
     CK(cudaGraphLaunch(exec, s));
-    c->launches += (2 + 2 * nfs::plane_pass_kernels<R>(c->n1)) * kCgChunk;
+    c->launches += (nfs::product_kernels<R>(c->n1) + (nfs::cg_fusable<R>(c->n1) ? 0 : 1)) * kCgChunk;
     CK(cudaMemcpy2DAsync(c->st_host, sizeof(CGState), c->st, sizeof(CGState), head, c->P, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     bool all = true;
@@ -1075,7 +1098,7 @@ void free_ctx(nfs_ctx* c) {
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
                   c->mat64, c->mat32, c->basis64, c->bloch64, c->lamdf, c->twdf[0], c->twdf[1], c->twdf[2], c->matdf,
                   c->basisdf, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
-                  c->p32, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
+                  c->p32, c->p32b, c->Ap32, c->st, c->d_small, c->d_flags, c->dscratch, c->V, c->MV, c->V32, c->MV32,
                   c->MV32lo, c->dY, c->binv64, c->zv, c->gv, c->zY};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1352,6 +1375,7 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
     TRYC(dalloc(c, &c->r32, PN));
     TRYC(dalloc(c, &c->p32, PN));
     TRYC(dalloc(c, &c->Ap32, PN));
+    if (nfs::cg_needs_p_out<float>(n1)) TRYC(dalloc(c, &c->p32b, PN));
   }
   TRYC(dalloc(c, &c->st, P));
   CKC(cudaMallocHost((void**)&c->st_host, (size_t)P * sizeof(CGState)));
