@@ -90,7 +90,9 @@ typedef struct {
                             * smaller)                                          */
   int max_refine;          /* mixed: cap on FP64 refinement steps                 */
   double eig_tol;          /* Lanczos: Ritz residual <= eig_tol * |theta|         */
-  int ncv;                 /* Lanczos basis size; 0 means max(3 nev, 2 nev + 2)   */
+  int ncv;                 /* Lanczos basis size; > 0: fixed, and the basis is
+                            * allocated by nfs_setup; 0: max(3 nev, 2 nev + 2,
+                            * min(12 nev, 320)) (no restart for most solves)   */
   int max_restarts;        /* thick-restart cap                                   */
   double orth_tol;         /* Lanczos semi-orthogonality level: when the measured
                             * loss of A_r-orthogonality of a new vector to the
@@ -203,6 +205,24 @@ int nfs_cg_solve(nfs_ctx* ctx, const void* b, void* x, nfs_solve_info* info);
  * NULL.  info may be NULL.  Returns NFS_ENOCONV (results still written) if the
  * restart cap is hit first. */
 int nfs_eigs(nfs_ctx* ctx, int nev, double* omega, void* Y, nfs_eigs_info* info);
+
+/* Residuals of eigenpairs of the HHPD-NFGEP B_r y = omega^{-1} A_r y
+ * (thm:NFSEP_real_ew; eq. NFSEP_spd_1 for B_r):
+ *   res[j] = || A_r y_j - omega_j B_r y_j ||_2 / || y_j ||_2   (scale-free),
+ * with the complex128 product and B_r on the device, FP64 sums.
+ *   omega: HOST, m doubles.  Y: DEVICE complex128 [m][4n] (as nfs_eigs
+ *   writes it).  res: HOST, m doubles.
+ * Synchronises the context's work stream.  Single-problem contexts only. */
+int nfs_residuals(nfs_ctx* ctx, int m, const double* omega, const void* Y, double* res);
+
+/* Allocate now the device memory an nfs_eigs(ctx, nev, ...) call uses (the
+ * Lanczos basis of opt.ncv, or of the default size for nev, its shadows, the
+ * reduction scratch and the restart rotation matrix), so that the eigensolve
+ * itself allocates nothing.  Contexts set up with opt.ncv > 0 have it already.
+ * The default size depends on nev only, never on the free device memory:
+ * NFS_ENOMEM when it does not fit (choose a smaller opt.ncv, e.g. the paper's
+ * 3 nev).  A later nfs_eigs with a larger basis reallocates. */
+int nfs_reserve(nfs_ctx* ctx, int nev);
 
 /* Gradient of sum_j weights[j] * omega_j with respect to every per-component
  * permittivity and chirality value, from eigenvectors Y (device complex128

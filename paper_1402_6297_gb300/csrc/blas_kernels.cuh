@@ -66,6 +66,27 @@ k_dot_re(const C* __restrict__ x, const C* __restrict__ y, long long N, double* 
   if (threadIdx.x == 0) part[(long long)p * pstride + blockIdx.x] = s;
 }
 
+// Partials of |Ay - omega By|^2 and |y|^2 for one eigenpair (the residual
+// of the HHPD-NFGEP, B_r y = omega^{-1} A_r y scaled by omega): block b writes
+// part[2b], part[2b + 1]; grid kRedBlocks.
+__global__ void __launch_bounds__(kRedThreads)
+k_residual_parts(const double2* __restrict__ Ay, const double2* __restrict__ By, const double2* __restrict__ y,
+                 double omega, long long N, double* __restrict__ part) {
+  double rr = 0.0, yy = 0.0;
+  for (long long i = (long long)blockIdx.x * kRedThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kRedThreads) {
+    const double2 a = Ay[i], b = By[i], v = y[i];
+    const double dx = a.x - omega * b.x, dy = a.y - omega * b.y;
+    rr += dx * dx + dy * dy;
+    yy += v.x * v.x + v.y * v.y;
+  }
+  rr = block_sum<kRedThreads>(rr);
+  yy = block_sum<kRedThreads>(yy);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rr;
+    part[2 * blockIdx.x + 1] = yy;
+  }
+}
+
 // CG start, one block per problem: rr = sum part_a; stop once r^* r <= tol2[p].
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_init(CGState* st, const double* __restrict__ tol2, int maxit, int npart_a) {
@@ -238,7 +259,7 @@ __global__ void k_axpy_promote(double2* __restrict__ x, const double* __restrict
 // (eq. NFSEP_spd_1).  lam holds Lambda_1 | Lambda_2 | Lambda_3 per problem
 // (stride n1 + n2 + n3); v and out hold P vectors of 4n.
 __global__ void k_apply_Br(const double2* __restrict__ v, double2* __restrict__ out, const double2* __restrict__ lam,
-                           int n1, int n2, int n3, int P) {
+                           int n1, int n2, int n3, int P, long long vstride = -1) {
   const long long n = (long long)n1 * n2 * n3;
   const int nl = n1 + n2 + n3;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n * P; g += (long long)gridDim.x * blockDim.x) {
@@ -249,7 +270,7 @@ __global__ void k_apply_Br(const double2* __restrict__ v, double2* __restrict__ 
     const double2* L = lam + p * nl;
     const double lq = cabs2(L[i1]) + cabs2(L[n1 + i2]) + cabs2(L[n1 + n2 + i3]);
     const double is = 1.0 / sqrt(lq);
-    const double2* vp = v + p * 4 * n;
+    const double2* vp = v + p * (vstride >= 0 ? vstride : 4 * n);  // problem p's input (e.g. a basis column)
     double2* op = out + p * 4 * n;
     const double2 v1a = vp[e], v1b = vp[n + e], v2a = vp[2 * n + e], v2b = vp[3 * n + e];
     op[e] = cmul_i(cscale(v2a, is));

@@ -627,7 +627,12 @@ int multi_axpy(nfs_ctx* c, double2* w, double2* Mw, int j0, int m, const std::ve
 int exact_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, const int* d_active) {
   cudaStream_t s = c->work;
   const long long vstride = (long long)c->vcap * c->N;
-  constexpr int G = 4;
+  // basis vectors per block: each block streams its slice of w once per G
+  // vectors, so a larger G re-reads w less often
+#ifndef NFS_EXACT_G
+#define NFS_EXACT_G 4
+#endif
+  constexpr int G = NFS_EXACT_G;
   double* part = c->dscratch;
   double* fin = c->dscratch + off_fin(c);
   // w split once into floats (the CG work vectors x32 / r32 are free here)
@@ -700,12 +705,10 @@ int rotate(nfs_ctx* c, double2* base, int m, const std::vector<double>& Y, int k
 // B_r applied to basis vector j of every problem -> out (P x N); t64 is used
 // to gather the vectors contiguously
 int apply_Br_basis(nfs_ctx* c, int j, double2* out) {
+  // B_r of basis column j of every problem, read in place (stride vcap N)
   const long long vstride = (long long)c->vcap * c->N;
-  for (int p = 0; p < c->P; ++p)
-    CK(cudaMemcpyAsync(c->t64 + (long long)p * c->N, c->V + p * vstride + (long long)j * c->N,
-                       c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->work));
-  nfs::k_apply_Br<<<grid_blocks(c->n * c->P, 256), 256, 0, c->work>>>(c->t64, out, c->lam64, c->n1, c->n2, c->n3,
-                                                                      c->P);
+  nfs::k_apply_Br<<<grid_blocks(c->n * c->P, 256), 256, 0, c->work>>>(c->V + (long long)j * c->N, out, c->lam64,
+                                                                      c->n1, c->n2, c->n3, c->P, vstride);
   CK(cudaGetLastError());
   c->launches += 1;
   return NFS_OK;
@@ -718,29 +721,46 @@ double basis_bytes_per_vector(const nfs_ctx* c) { return (double)c->P * c->N * (
 int wanted_ncv(int nev) { return std::max(std::max(3 * nev, 2 * nev + 2), std::min(12 * nev, 320)); }
 
 // Default basis size: generous (device memory is plentiful and restarts cost
-// FP64 basis rotations), capped by half of the free device memory.
+// FP64 basis rotations and accuracy), a fixed function of nev: the same
+// basis, the same iterates and the same speed whatever else holds the GPU.
+// NFS_ENOMEM when it does not fit (set opt.ncv smaller, e.g. the paper's
+// 3 nev).
 int default_ncv(nfs_ctx* c, int nev) {
   if (c->ncv_set > 0) return c->ncv_set;
-  int m = wanted_ncv(nev);
-  size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
-    const int cap = (int)std::max(0.0, 0.5 * (double)fr / basis_bytes_per_vector(c)) - 1;
-    if (cap < m) m = std::max(cap, 2 * nev + 2);
-  }
-  return m;
+  return wanted_ncv(nev);
 }
 
 // Thick-restart invert Lanczos on (B_r, A_r) for every problem of the
 // context, in lock-step, on the work stream.  omega: host P x nev; Y: device
 // P x nev x N or null; infos: P entries or null.  Returns the worst status.
+// The Lanczos basis size for nev wanted pairs, and the device memory that an
+// eigensolve of that size uses (basis, its shadows, reduction scratch, the
+// restart rotation matrix), allocated here once: an eigensolve within an
+// earlier reservation allocates nothing.
+int lanczos_size(nfs_ctx* c, int nev) {
+  int m = c->opt.ncv > 0 ? c->opt.ncv : default_ncv(c, nev);
+  return (int)std::min<long long>(m, c->N - 1);
+}
+int reserve_lanczos(nfs_ctx* c, int m) {
+  TRY(ensure_basis(c, m));
+  TRY(ensure_scratch(c, lanczos_scratch_len(c->P, c->vcap)));
+  const size_t need = (size_t)c->P * m * m;  // rotate(): m x keep and k x nev, both <= m x m
+  if (c->dY_len < need) {
+    if (c->dY) cudaFree(c->dY);
+    c->dY = nullptr;
+    c->dY_len = 0;
+    TRY(dalloc(c, &c->dY, need));
+    c->dY_len = need;
+  }
+  return NFS_OK;
+}
+
 int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* infos) {
   const int P = c->P;
   const long long N = c->N;
-  int m = c->opt.ncv > 0 ? c->opt.ncv : default_ncv(c, nev);
-  m = (int)std::min<long long>(m, N - 1);
+  const int m = lanczos_size(c, nev);
   if (m <= nev + 1) return NFS_EINVAL;
-  TRY(ensure_basis(c, m));
-  TRY(ensure_scratch(c, lanczos_scratch_len(P, c->vcap)));
+  TRY(reserve_lanczos(c, m));
   const long long vstride = (long long)c->vcap * N;
   cudaStream_t s = c->work;
   const long long mv32_0 = c->mv32, mv64_0 = c->mv64, launches_0 = c->launches;
@@ -1391,6 +1411,9 @@ int setup_class(nfs_ctx** out, int P, const int grid[3], const nfs_material* con
   if (o.precision == NFS_PREC_MIXED) CKC(nfs::matvec_prepare<nfs::df>(n1, n2, n3));
   CKC(nfs::grad_prepare(n1, n2, n3));
   CKC(nfs::fields_prepare(n1, n2, n3));
+  // an explicit basis size: the eigensolver's memory is taken here, so that
+  // no later call allocates
+  if (o.ncv > 0) TRYC(reserve_lanczos(c, (int)std::min<long long>(o.ncv, c->N - 1)));
   CKC(cudaDeviceSynchronize());
 #undef TRYC
 #undef CKC
@@ -1540,6 +1563,46 @@ extern "C" int nfs_cg_solve(nfs_ctx* c, const void* b, void* x, nfs_solve_info* 
     info->status = so.status[0];
   }
   return so.status[0];
+}
+
+extern "C" int nfs_residuals(nfs_ctx* c, int m, const double* omega, const void* Yv, double* res) {
+  if (!c || m <= 0 || !omega || !Yv || !res) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;
+  if (c->P != 1) return NFS_EUNSUPPORTED;
+  if ((uintptr_t)Yv & 15) return NFS_EINVAL;
+  TRY(join_caller(c));
+  cudaStream_t s = c->work;
+  const long long n = c->n, N = c->N;
+  const double2* Y = (const double2*)Yv;
+  for (int j = 0; j < m; ++j) {
+    const double2* y = Y + (long long)j * N;
+    // A_r y (complex128 product) and B_r y, then |A_r y - omega B_r y| / |y|
+    TRY(matvec<double>(c, s, y, c->t64b));
+    nfs::k_apply_Br<<<grid_blocks(n, 256), 256, 0, s>>>(y, c->t64, c->lam64, c->n1, c->n2, c->n3, 1);
+    nfs::k_residual_parts<<<kRedBlocks, kRedThreads, 0, s>>>(c->t64b, c->t64, y, omega[j], N, c->dscratch);
+    CK(cudaGetLastError());
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->hscratch, c->dscratch, (size_t)2 * kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double rr = 0.0, yy = 0.0;
+    for (int b = 0; b < kRedBlocks; ++b) {
+      rr += c->hscratch[2 * b];
+      yy += c->hscratch[2 * b + 1];
+    }
+    if (!(yy > 0.0)) return NFS_EINVAL;
+    res[j] = std::sqrt(rr / yy);
+  }
+  return NFS_OK;
+}
+
+extern "C" int nfs_reserve(nfs_ctx* c, int nev) {
+  if (!c || nev <= 0 || nev >= c->N / 2) return NFS_EINVAL;
+  if (c->binv64) return NFS_EUNSUPPORTED;
+  const int m = lanczos_size(c, nev);
+  if (m <= nev + 1) return NFS_EINVAL;
+  TRY(reserve_lanczos(c, m));
+  CK(cudaDeviceSynchronize());
+  return NFS_OK;
 }
 
 extern "C" int nfs_eigs(nfs_ctx* c, int nev, double* omega, void* Y, nfs_eigs_info* info) {

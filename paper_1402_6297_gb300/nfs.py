@@ -47,6 +47,7 @@ EXPORTED = (
     "nfs_setup_batch", "nfs_eigs_batch", "nfs_batch_num_classes", "nfs_destroy_batch",
     "nfs_eig_fields", "nfs_gep_residual", "nfs_band_structure",
     "nfs_setup_biiso", "nfs_nfsep_matvec", "nfs_nfsep_eigs", "nfs_nfsep_fields",
+    "nfs_residuals", "nfs_reserve",
 )
 NOALLOC_MAX_VOXELS = 32768
 
@@ -180,6 +181,10 @@ def lib():
     L.nfs_cg_solve.restype = ip
     L.nfs_eigs.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(EigsInfo)]
     L.nfs_eigs.restype = ip
+    L.nfs_reserve.argtypes = [vp, ip]
+    L.nfs_reserve.restype = ip
+    L.nfs_residuals.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, ctypes.POINTER(ctypes.c_double)]
+    L.nfs_residuals.restype = ip
     L.nfs_eig_grad.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double), vp, vp, vp]
     L.nfs_eig_grad.restype = ip
     L.nfs_eig_fields.argtypes = [vp, ip, vp, vp]
@@ -271,6 +276,14 @@ def _current_stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+_live_contexts = 0  # Context objects whose library context is open
+
+
+def live_contexts():
+    """How many Context objects currently hold an open library context."""
+    return _live_contexts
+
+
 class Context:
     """One Bloch problem on the GPU: grid, k, medium, options (nfs_setup)."""
 
@@ -301,6 +314,8 @@ class Context:
                "nfs_setup")
         self.h = h
         self._torch = torch
+        global _live_contexts
+        _live_contexts += 1
 
     # -- helpers --------------------------------------------------------------
     def _vec(self, t, dtype):
@@ -314,6 +329,8 @@ class Context:
         if getattr(self, "h", None):
             lib().nfs_destroy(self.h)
             self.h = None
+            global _live_contexts
+            _live_contexts -= 1
 
     def __del__(self):
         try:
@@ -378,6 +395,10 @@ class Context:
         if code not in (NFS_OK, NFS_ENOCONV):
             raise NFSError(code, "nfs_cg_solve")
         return x, info
+
+    def reserve(self, nev):
+        """Allocate now what an eigensolve for nev pairs uses (nfs_reserve)."""
+        _check(lib().nfs_reserve(self.h, int(nev)), "nfs_reserve")
 
     def eigs(self, nev, vectors=True, allow_noconv=False):
         torch = self._torch
@@ -671,10 +692,16 @@ def matvec_noalloc(grid, kdota, kind, axes, eps, gamma, u, out, alpha=2.0, beta=
 
 
 def residuals(ctx: Context, omega, Y):
-    """||A_r y - omega B_r y|| / ||y|| per eigenpair (FP64, through the ABI)."""
-    out = []
-    for j in range(len(omega)):
-        y = Y[j].contiguous()
-        r = ctx.matvec(y) - float(omega[j]) * ctx.apply_Br(y)
-        out.append(float(r.norm() / y.norm()))
-    return out
+    """||A_r y - omega B_r y|| / ||y|| per eigenpair (nfs_residuals: FP64 on
+    the device)."""
+    torch = ctx._torch
+    m = len(omega)
+    if m == 0:
+        return []
+    Yc = Y.contiguous()
+    if not (Yc.is_cuda and Yc.dtype == torch.complex128 and Yc.numel() == m * 4 * ctx.n):
+        raise ValueError("Y: CUDA complex128 tensor of m x 4n")
+    om = (ctypes.c_double * m)(*[float(w) for w in omega])
+    res = (ctypes.c_double * m)()
+    _check(lib().nfs_residuals(ctx.h, m, om, ctypes.c_void_p(Yc.data_ptr()), res), "nfs_residuals")
+    return [float(x) for x in res]

@@ -142,6 +142,8 @@ def test_null_handles_rejected(nfs):
     assert L.nfs_cg_solve(None, None, None, None) == nfs.NFS_EINVAL
     assert L.nfs_eigs(None, 3, None, None, None) == nfs.NFS_EINVAL
     assert L.nfs_eig_grad(None, 1, None, None, None, None) == nfs.NFS_EINVAL
+    assert L.nfs_reserve(None, 3) == nfs.NFS_EINVAL
+    assert L.nfs_residuals(None, 1, None, None, None) == nfs.NFS_EINVAL
     L.nfs_destroy(None)
 
 

@@ -159,3 +159,35 @@ def test_deflation_checks_find_degenerate_copies(nfs, precision):
     res = nfs.residuals(ctx, omega, Y)
     assert max(res) < 1e-8
     ctx.close()
+
+
+def test_residuals_call_matches_oracle(nfs):
+    # nfs_residuals against the oracle's ||A_r y - omega B_r y|| / ||y|| for
+    # eigenpairs whose omega is perturbed by a known amount (so the residual
+    # is far above rounding): same definition, two independent evaluations
+    w = wl.workload("sphere8")
+    ctx = nfs.Context(w["grid"], w["kdota"], w["medium"], precision="fp64")
+    omega, Y, _ = ctx.eigs(4)
+    om_p = omega * (1.0 + 1e-3 * np.arange(1, 5))
+    got = nfs.residuals(ctx, om_p, Y)
+    O = nfgep.NFGEP(w["grid"], w["kdota"], w["medium"])
+    Yh = Y.cpu().numpy()
+    ref = [O.residual(om_p[j], Yh[j]) for j in range(4)]
+    assert np.allclose(got, ref, rtol=1e-9, atol=0), (got, ref)
+    ctx.close()
+
+
+def test_reserve_then_eigs_allocates_nothing(nfs):
+    w = wl.workload("sphere8")
+    ctx = nfs.Context(w["grid"], w["kdota"], w["medium"], precision="mixed")
+    ctx.reserve(6)
+    before = ctx.device_bytes
+    ctx.eigs(6)
+    assert ctx.device_bytes == before
+    ctx.close()
+    # an explicit basis size: the basis is taken by nfs_setup itself
+    ctx = nfs.Context(w["grid"], w["kdota"], w["medium"], precision="mixed", ncv=18)
+    before = ctx.device_bytes
+    ctx.eigs(6)
+    assert ctx.device_bytes == before
+    ctx.close()

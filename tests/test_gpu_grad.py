@@ -110,3 +110,26 @@ def test_uniform_direction_derivative_128(lib):
         c2.close()
     fd = (f[0] - f[1]) / (2 * h)
     assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
+
+
+def test_library_context_released_without_backward(ag, lib):
+    # inference (no_grad) keeps nothing; a forward whose output is dropped
+    # before backward releases its context with the graph
+    import gc
+    g = (8, 8, 8)
+    med = wl.chiral_sphere(g)
+    eps = torch.tensor(med.eps[0], dtype=torch.float64, requires_grad=True)
+    gam = torch.tensor(med.gamma[0], dtype=torch.float64, requires_grad=True)
+    gc.collect()
+    before = lib.live_contexts()
+    with torch.no_grad():
+        om = ag.chiral_eigenvalues(eps, gam, g, K, nev=3)
+    assert lib.live_contexts() == before
+    om = ag.chiral_eigenvalues(eps, gam, g, K, nev=3)
+    assert lib.live_contexts() == before + 1
+    del om
+    gc.collect()
+    assert lib.live_contexts() == before
+    om = ag.chiral_eigenvalues(eps, gam, g, K, nev=3)
+    om.sum().backward()
+    assert lib.live_contexts() == before
