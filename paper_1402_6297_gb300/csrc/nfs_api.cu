@@ -29,6 +29,7 @@
 #include "blas_kernels.cuh"
 #include "dfloat.cuh"
 #include "host_eig.h"
+#include "host_zeig.h"
 #include "krylov.h"
 #include "matvec.h"
 #include "nfsep.h"
@@ -730,6 +731,139 @@ int default_ncv(nfs_ctx* c, int nev) {
   return wanted_ncv(nev);
 }
 
+// Rayleigh-Ritz over the nev Ritz vectors of problem p (basis positions
+// 0..nev-1 after a rotation): the pencil H z = theta G z with
+// H = Y^* B_r Y and G = Y^* A_r Y (A_r Y from fresh products), formed with
+// FP64 inner products and solved on the host (Cholesky of G, Schur form of the
+// Hermitian L^-1 H L^-*).  Copies of a degenerate eigenvalue found by
+// deflation checks were each converged against locked vectors that are only
+// accurate to eig_tol, so their eigenvalues carry a first-order error; the
+// Rayleigh quotients on the span of all nev vectors are accurate to second
+// order.  theta: ascending order of omega = 1/theta on return; z: the
+// row-major nev x nev complex coefficients (interleaved re, im), columns in
+// that order.  flags: a device mask with problem p alone set.
+int final_rayleigh_ritz(nfs_ctx* c, int p, int nev, const int* flags, std::vector<double>& theta,
+                        std::vector<double>& z, int kout = -1) {
+  using cplxd = std::complex<double>;
+  const long long N = c->N, vstride = (long long)c->vcap * N;
+  if (kout < 0) kout = nev;
+  std::vector<cplxd> H((size_t)nev * nev), G((size_t)nev * nev);
+  std::vector<double> d;
+  // A_r y_i from fresh products (complex128, or double-single in mixed
+  // contexts) of problem p alone
+  std::vector<int> skip(c->P, 1);
+  skip[p] = 0;
+  TRY(put_flags(c, c->work, 2 * c->P, skip));
+  const int* d_skip = c->d_flags + 2 * c->P;
+  for (int i = 0; i < nev; ++i) {
+    TRY(apply_Br_basis(c, i, c->t64));  // B_r y_i (every problem; p's is used)
+    TRY(multi_dot(c, c->V, 0, nev, c->t64, d, flags));
+    for (int j = 0; j < nev; ++j) H[(size_t)j * nev + i] = cplxd(d[(size_t)p * 2 * nev + 2 * j], d[(size_t)p * 2 * nev + 2 * j + 1]);
+    CK(cudaMemcpyAsync(c->t64 + (long long)p * N, c->V + p * vstride + (long long)i * N, N * sizeof(double2),
+                       cudaMemcpyDeviceToDevice, c->work));
+    if (c->lamdf)
+      TRY(matvec_refine(c, c->work, c->t64, c->t64b, d_skip, 1));
+    else
+      TRY(matvec<double>(c, c->work, c->t64, c->t64b, d_skip, 1));
+    TRY(multi_dot(c, c->V, 0, nev, c->t64b, d, flags));
+    for (int j = 0; j < nev; ++j) G[(size_t)j * nev + i] = cplxd(d[(size_t)p * 2 * nev + 2 * j], d[(size_t)p * 2 * nev + 2 * j + 1]);
+  }
+  // symmetrise (the inner products are exact only to rounding)
+  for (int i = 0; i < nev; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const cplxd h = 0.5 * (H[(size_t)i * nev + j] + std::conj(H[(size_t)j * nev + i]));
+      const cplxd g = 0.5 * (G[(size_t)i * nev + j] + std::conj(G[(size_t)j * nev + i]));
+      H[(size_t)i * nev + j] = h;
+      H[(size_t)j * nev + i] = std::conj(h);
+      G[(size_t)i * nev + j] = g;
+      G[(size_t)j * nev + i] = std::conj(g);
+    }
+  // G = L L^*
+  std::vector<cplxd> L((size_t)nev * nev, 0.0);
+  for (int j = 0; j < nev; ++j) {
+    double dj = G[(size_t)j * nev + j].real();
+    for (int q = 0; q < j; ++q) dj -= std::norm(L[(size_t)j * nev + q]);
+    if (!(dj > 0)) {
+      if (trace_lanczos())
+        std::fprintf(stderr, "nfs rayleigh-ritz: problem %d, Gram matrix of %d vectors not positive at %d (%.3e)\n", p,
+                     nev, j, dj);
+      return NFS_EBREAKDOWN;
+    }
+    const double ljj = std::sqrt(dj);
+    L[(size_t)j * nev + j] = ljj;
+    for (int i = j + 1; i < nev; ++i) {
+      cplxd v = G[(size_t)i * nev + j];
+      for (int q = 0; q < j; ++q) v -= L[(size_t)i * nev + q] * std::conj(L[(size_t)j * nev + q]);
+      L[(size_t)i * nev + j] = v / ljj;
+    }
+  }
+  // M = L^-1 H L^-*: forward substitution on the columns of H, then on the
+  // columns of (L^-1 H)^*
+  auto lsolve = [&](std::vector<cplxd>& X) {  // X <- L^-1 X, X row-major nev x nev
+    for (int col = 0; col < nev; ++col)
+      for (int i = 0; i < nev; ++i) {
+        cplxd v = X[(size_t)i * nev + col];
+        for (int q = 0; q < i; ++q) v -= L[(size_t)i * nev + q] * X[(size_t)q * nev + col];
+        X[(size_t)i * nev + col] = v / L[(size_t)i * nev + i];
+      }
+  };
+  std::vector<cplxd> M = H;
+  lsolve(M);
+  std::vector<cplxd> Mh((size_t)nev * nev);
+  for (int i = 0; i < nev; ++i)
+    for (int j = 0; j < nev; ++j) Mh[(size_t)i * nev + j] = std::conj(M[(size_t)j * nev + i]);
+  lsolve(Mh);  // = L^-1 (L^-1 H)^* = (L^-1 H L^-*)^* = L^-1 H L^-* (Hermitian)
+  std::vector<cplxd> Q;
+  if (!nfs::host::complex_schur(nev, Mh, Q)) return NFS_EBREAKDOWN;
+  // eigenvalues on the (real) diagonal; order by theta descending = omega ascending
+  std::vector<int> ord(nev);
+  for (int i = 0; i < nev; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(),
+            [&](int a, int b) { return Mh[(size_t)a * nev + a].real() > Mh[(size_t)b * nev + b].real(); });
+  theta.assign(kout, 0.0);
+  z.assign((size_t)2 * nev * kout, 0.0);
+  // z = L^-* Q: back substitution with L^* on each column of Q
+  for (int o = 0; o < kout; ++o) {
+    const int col = ord[o];
+    theta[o] = Mh[(size_t)col * nev + col].real();
+    std::vector<cplxd> x(nev);
+    for (int i = nev - 1; i >= 0; --i) {
+      cplxd v = Q[(size_t)i * nev + col];
+      for (int q = i + 1; q < nev; ++q) v -= std::conj(L[(size_t)q * nev + i]) * x[q];
+      x[i] = v / L[(size_t)i * nev + i];
+    }
+    for (int r = 0; r < nev; ++r) {
+      z[2 * ((size_t)r * kout + o)] = x[r].real();
+      z[2 * ((size_t)r * kout + o) + 1] = x[r].imag();
+    }
+  }
+  return NFS_OK;
+}
+
+// Complex rotation V_p[0:k] = V_p[0:q] z (z: q x k row-major, interleaved) of
+// problem p's V and MV through the device copy of z.
+int zrotate_basis(nfs_ctx* c, int p, int q, int k, const std::vector<double>& z, bool with_mv) {
+  const long long vstride = (long long)c->vcap * c->N;
+  if (c->dY_len < z.size()) {
+    if (c->dY) cudaFree(c->dY);
+    c->dY = nullptr;
+    c->dY_len = 0;
+    TRY(dalloc(c, &c->dY, z.size()));
+    c->dY_len = z.size();
+  }
+  CK(cudaMemcpyAsync(c->dY, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice, c->work));
+  CK(nfs::zrotate(c->V + p * vstride, q, c->dY, k, c->N, c->work));
+  if (with_mv) CK(nfs::zrotate(c->MV + p * vstride, q, c->dY, k, c->N, c->work));
+  CK(cudaStreamSynchronize(c->work));
+  c->launches += with_mv ? 2 : 1;
+  return NFS_OK;
+}
+
+// Largest loss of A_r-orthogonality removed with the FP32 shadow update; a
+// larger one is removed in FP64 (the shadow update's rounding, ~6e-8 of the
+// coefficients, would otherwise reappear above orth_tol).
+constexpr double kShadowMaxLoss = 1e-6;
+
 // Thick-restart invert Lanczos on (B_r, A_r) for every problem of the
 // context, in lock-step, on the work stream.  omega: host P x nev; Y: device
 // P x nev x N or null; infos: P entries or null.  Returns the worst status.
@@ -793,6 +927,7 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
   std::vector<std::vector<double>> H(P, std::vector<double>((size_t)m * m, 0.0));
   std::vector<double> beta_last(P, 0.0);
   std::vector<int> active(P, 1), jm(P, 0), nconv(P, 0), steps(P, 0), restarts_p(P, 0), reorths(P, 0);
+  std::vector<int> full_reorths(P, 0);  // steps that needed the FP64 fallback
   std::vector<long long> cg_total(P, 0);
   std::vector<int> status(P, NFS_OK);
   int jstart = 0, local_lo = 0, restarts = 0;
@@ -827,6 +962,13 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       TRY(solve(c, Mw, w, true, active, so));
       CK(cudaStreamSynchronize(s));
       c->sec_solve += now_s() - ts;
+      // A_r w = B_r v_j - r with r the solve's final residual (the refined
+      // FP64 residual in mixed contexts): the right-hand side alone would
+      // carry the residual into A_r V, where the recurrence amplifies it like
+      // the Lanczos polynomials; on long runs over degenerate spectra that
+      // drift corrupted the orthogonality measure, the re-orthogonalisation
+      // and the projected matrix
+      TRY(sub64(c, s, Mw, c->r64, Mw));
       for (int p = 0; p < P; ++p) {
         if (!active[p]) continue;
         if (so.status[p] == NFS_EBREAKDOWN) {
@@ -845,7 +987,20 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       TRY(multi_dot(c, c->MV, local_lo, nl, w, coef, d_active));
       TRY(multi_axpy(c, w, Mw, local_lo, nl, coef, d_active));
       std::vector<double> alpha(P);
-      for (int p = 0; p < P; ++p) alpha[p] = coef[(size_t)p * 2 * nl + 2 * (j - local_lo)];
+      for (int p = 0; p < P; ++p) {
+        alpha[p] = coef[(size_t)p * 2 * nl + 2 * (j - local_lo)];
+        if (!active[p]) continue;
+        // the first step after a thick restart (or of a deflation check):
+        // the couplings of the continuation vector to the kept (or locked)
+        // vectors as measured, v_i^* B_r v_j, instead of their values in exact
+        // arithmetic (beta times the last row of the Ritz vectors, or zero).
+        // On long runs over degenerate spectra the two drift apart, and the
+        // projected matrix must be the projection the orthogonalisation used
+        // (else spurious Ritz values appear, even outside the spectrum).
+        if (local_lo == 0 && j == jstart && j > 0)
+          for (int i = 0; i < j; ++i)
+            H[p][(size_t)i * m + j] = H[p][(size_t)j * m + i] = coef[(size_t)p * 2 * nl + 2 * i];
+      }
       TRY(dots_re(c, s, w, Mw, bb));
       const std::vector<double> bb_recur = bb;
       std::vector<double> loss_first(P, 0.0);
@@ -856,13 +1011,14 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       // inner products (double-single arithmetic on the split shadows); when
       // it exceeds orth_tol, remove those components (the vectors [local_lo,
       // j] were just orthogonalised in FP64 by the recurrence).  The update
-      // is formed in FP32, exact enough while the coefficients are small; a
-      // large loss (a coupling after a restart) takes a second pass.
+      // is formed in FP32, exact enough while the coefficients are small
+      // (loss <= kShadowMaxLoss); a larger loss is removed in FP64, and a
+      // very large one (a coupling after a restart) takes a second pass.
       if (local_lo > 0) {
         std::vector<int> reorth(P, 0);
         for (int pass = 0; pass < 3; ++pass) {
           TRY(exact_dots(c, local_lo, w, d, d_active));
-          bool any_re = false, big = false;
+          bool any_re = false, big = false, big_loss = false;
           for (int p = 0; p < P; ++p) {
             reorth[p] = 0;
             if (!active[p]) continue;
@@ -874,14 +1030,25 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
             reorth[p] = pass == 0 ? loss > c->opt.orth_tol : loss > 1e-3 * c->opt.orth_tol + 1e-13;
             any_re = any_re || reorth[p];
             big = big || (reorth[p] && loss > 1e-3);
+            big_loss = big_loss || (reorth[p] && loss > kShadowMaxLoss);
             if (reorth[p] && pass == 0) ++reorths[p];
           }
           if (!any_re) break;
           TRY(put_flags(c, s, P, reorth));
-          nfs::k_shadow_axpy<<<dim3(grid_blocks(N, 256), P), 256, (size_t)local_lo * sizeof(float2), s>>>(
-              w, Mw, c->V32, c->MV32, vstride, c->dscratch + off_fin(c), local_lo, N, c->d_flags + P);
-          CK(cudaGetLastError());
-          c->launches += 1;
+          if (big_loss) {
+            // a loss this large would come back from an FP32 update (its
+            // rounding is ~6e-8 of the coefficients): remove the components
+            // in FP64, with coefficients v_i^* A_r w from the stored A_r V
+            TRY(multi_dot(c, c->MV, 0, local_lo, w, coef2, c->d_flags + P));
+            TRY(multi_axpy(c, w, Mw, 0, local_lo, coef2, c->d_flags + P));
+            for (int p = 0; p < P; ++p)
+              if (reorth[p]) ++full_reorths[p];
+          } else {
+            nfs::k_shadow_axpy<<<dim3(grid_blocks(N, 256), P), 256, (size_t)local_lo * sizeof(float2), s>>>(
+                w, Mw, c->V32, c->MV32, vstride, c->dscratch + off_fin(c), local_lo, N, c->d_flags + P);
+            CK(cudaGetLastError());
+            c->launches += 1;
+          }
           TRY(dots_re(c, s, w, Mw, bb));
           if (!big) break;
         }
@@ -891,8 +1058,8 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
         for (int p = 0; p < P; ++p)
           if (active[p])
             std::fprintf(stderr, "nfs lanczos: problem %d step %d (j %d, lo %d): alpha %.17e beta2 %.6e -> %.6e "
-                         "loss %.3e cg %d relres %.3e\n", p, steps[p], j, local_lo, alpha[p], bb_recur[p], bb[p],
-                         loss_first[p], so.iters[p], so.relres[p]);
+                         "loss %.3e cg %d relres %.3e fp64-reorth %d\n", p, steps[p], j, local_lo, alpha[p],
+                         bb_recur[p], bb[p], loss_first[p], so.iters[p], so.relres[p], full_reorths[p]);
       for (int p = 0; p < P; ++p) {
         if (!active[p]) continue;
         if (!(bb[p] > 0)) return NFS_EBREAKDOWN;
@@ -1065,7 +1232,28 @@ int eigs_core(nfs_ctx* c, int nev, double* omega, double2* Y, nfs_eigs_info* inf
       omega[(size_t)p * nev + i] = 1.0 / theta[cc];
       maxres = std::max(maxres, std::fabs(beta_last[p] * Z[(size_t)(k - 1) * k + cc]) / std::fabs(theta[cc]));
     }
-    if (Y) {
+    if (status[p] == NFS_OK) {
+      // a Rayleigh-Ritz on the span of the nev Ritz vectors with the true
+      // inner products: second-order accurate eigenvalues for copies found by
+      // deflation checks, and values that stay inside the spectrum even where
+      // the basis has lost A_r-orthogonality
+      std::vector<double> Ycm((size_t)P * k * nev, 0.0);
+      for (int i = 0; i < nev; ++i)
+        for (int r = 0; r < k; ++r) Ycm[(size_t)p * k * nev + (size_t)i * k + r] = Z[(size_t)r * k + (k - 1 - i)];
+      std::fill(one.begin(), one.end(), 0);
+      one[p] = 1;
+      TRY(put_flags(c, s, P, one));
+      TRY(rotate(c, c->V, k, Ycm, nev, c->d_flags + P));
+      std::vector<double> th2, zc;
+      TRY(final_rayleigh_ritz(c, p, nev, c->d_flags + P, th2, zc));
+      for (int i = 0; i < nev; ++i) omega[(size_t)p * nev + i] = 1.0 / th2[i];
+      TRY(zrotate_basis(c, p, nev, nev, zc, false));
+      if (Y) {
+        CK(cudaMemcpyAsync(Y + (long long)p * nev * N, col(c->V, p, 0), (size_t)nev * N * sizeof(double2),
+                           cudaMemcpyDeviceToDevice, s));
+        CK(cudaStreamSynchronize(s));
+      }
+    } else if (Y) {
       // Ritz vectors of problem p: rotate its basis (only p flagged), then copy
       std::vector<double> Ycm((size_t)P * k * nev, 0.0);
       for (int i = 0; i < nev; ++i)

@@ -52,7 +52,9 @@ def test_homogeneous_dispersion(lib):
     # equal eigenvalues on these lines: a single start vector holds one copy
     # of each, so the solve needs up to seven deflation checks.  A copy found
     # by a check is converged against locked vectors that are themselves only
-    # converged to eig_tol (1e-10), not exact: measured up to 1e-8 relative.
+    # converged to eig_tol; the final Rayleigh-Ritz over all nev Ritz vectors
+    # makes every eigenvalue second-order accurate again: the FP64 bar of
+    # 1e-10 holds.
     omega, infos, _ = lib.band_structure(g, med, ks, 8, precision="fp64", deflation_checks=8)
     i3, i2, i1 = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
     for k, om in zip(ks, omega):
@@ -60,5 +62,26 @@ def test_homogeneous_dispersion(lib):
               + 4 * np.sin(np.pi * (i2 + k[1]) / n2) ** 2 * n2 ** 2
               + 4 * np.sin(np.pi * (i3 + k[2]) / n3) ** 2 * n3 ** 2).ravel()
         ref = np.sort(np.concatenate([np.sqrt(lq), np.sqrt(lq)]) / 2.0)[:8]
-        assert np.abs(om - ref).max() < 1e-7 * ref.max()
+        assert np.abs(om - ref).max() < 1e-10 * ref.max()
     assert max(i.deflation_checks for i in infos) >= 2
+
+
+def test_homogeneous_tight_tolerance_x_point(lib):
+    """A homogeneous medium at a k-point with four-fold degenerate clusters
+    and the tight Ritz tolerance 1e-12: many Lanczos steps after the wanted
+    pairs converge, where the A_r-orthogonality of the basis degrades fastest
+    (this case once returned NFS_EBREAKDOWN, later a spurious eigenvalue below
+    the spectrum).  omega = sqrt(Lambda_q) / 2, each twice (Section 5.1)."""
+    g = (16, 16, 16)
+    n1, n2, n3 = g
+    k = (0.5, 0.5, 5.0 / 12.0)
+    ctx = lib.Context(g, k, wl.homogeneous(g, eps=4.0), precision="fp64", eig_tol=1e-12, cg_tol=1e-13,
+                      deflation_checks=4)
+    om, _, info = ctx.eigs(8, vectors=False)
+    ctx.close()
+    i3, i2, i1 = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    lq = (4 * np.sin(np.pi * (i1 + k[0]) / n1) ** 2 * n1 ** 2
+          + 4 * np.sin(np.pi * (i2 + k[1]) / n2) ** 2 * n2 ** 2
+          + 4 * np.sin(np.pi * (i3 + k[2]) / n3) ** 2 * n3 ** 2).ravel()
+    ref = np.sort(np.concatenate([np.sqrt(lq), np.sqrt(lq)]) / 2.0)[:8]
+    assert np.abs(om - ref).max() < 1e-10 * ref.max(), (list(om), list(ref))
