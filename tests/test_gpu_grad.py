@@ -133,3 +133,98 @@ def test_library_context_released_without_backward(ag, lib):
     om = ag.chiral_eigenvalues(eps, gam, g, K, nev=3)
     om.sum().backward()
     assert lib.live_contexts() == before
+
+
+def test_oracle_pencil_gradient_16(lib):
+    """Config 5's oracle check at 16^3: d(omega_1 + ... + omega_5) / d(every
+    per-component eps and gamma) from the GPU's NFGEP adjoint against the
+    oracle's first-order perturbation of the Hermitian pencil K'' z = omega B'' z
+    (independent formulas), with the oracle's own eigenvectors: tier O3
+    (FFT NFGEP, ARPACK) y -> fields [E; H] of Algorithm 1's last step ->
+    z = [E; i H]."""
+    from oracle import nfgep
+    w = wl.workload("field16")
+    g, k, med = w["grid"], w["kdota"], w["medium"]
+    O = nfgep.NFGEP(g, k, med)
+    om_o, Y_o = O.eigs(6, tol=1e-12, cg_tol=1e-13)
+    assert om_o[4] < om_o[5] * (1 - 1e-6)  # the summed cluster is complete
+    n = O.n
+    Z = []
+    for j in range(5):
+        x = O.eigvec_fields(Y_o[:, j]).reshape(6, n)
+        Z.append(np.concatenate([x[:3].ravel(), 1j * x[3:].ravel()]))
+    re, rg = gep.pencil_gradient(med, om_o[:5], np.stack(Z, axis=1))
+    ctx = lib.Context(g, k, med, precision="fp64", eig_tol=1e-12, cg_tol=1e-13)
+    omega, Y, _ = ctx.eigs(6)
+    assert np.abs(omega[:5] - om_o[:5]).max() < 1e-10 * om_o[4]
+    d_eps, d_gam = ctx.eig_grad(Y[:5].contiguous(), np.ones(5))
+    ctx.close()
+    d_eps, d_gam = d_eps.cpu().numpy(), d_gam.cpu().numpy()
+    assert np.abs(d_eps - re).max() < 1e-6 * np.abs(re).max()
+    assert np.abs(d_gam - rg).max() < 1e-6 * np.abs(rg).max()
+
+
+def test_per_voxel_central_differences_64(lib):
+    """Config 5 at 64^3: the gradient of omega_1 + ... + omega_5 with respect to
+    the per-voxel eps (all three components of a voxel move together) on 32
+    random voxels against central differences with step h = 0.05 (the
+    readings' larger per-voxel step: d omega / d eps_v ~ omega / n, so a step
+    of 1e-6 would move omega below the eigensolver's accuracy; the O(h^2)
+    truncation of a single-voxel change scales with 1/n^2)."""
+    w = wl.workload("field64")
+    g, k, med = w["grid"], w["kdota"], w["medium"]
+    opts = dict(precision="mixed", cg_tol=1e-12, eig_tol=1e-12)
+    ctx = lib.Context(g, k, med, **opts)
+    omega, Y, _ = ctx.eigs(6)
+    assert omega[4] < omega[5] * (1 - 1e-6)
+    d_eps, _ = ctx.eig_grad(Y[:5].contiguous(), np.ones(5))
+    ctx.close()
+    grad_v = d_eps.sum(0).cpu().numpy()  # per voxel: the three components together
+    rng = np.random.default_rng(64)
+    h = 0.05
+    errs = []
+    for _ in range(32):
+        v = tuple(int(x) for x in rng.integers(0, 64, size=3))
+        f = []
+        for sgn in (1, -1):
+            e2 = med.eps.copy()
+            e2[(slice(None),) + v] += sgn * h
+            m2 = wl.Medium(med.grid, med.kind, e2, med.gamma, med.mu, med.axes)
+            c2 = lib.Context(g, k, m2, **opts)
+            om2, _, _ = c2.eigs(6, vectors=False)
+            c2.close()
+            f.append(float(om2[:5].sum()))
+        fd = (f[0] - f[1]) / (2 * h)
+        errs.append(abs(fd - grad_v[v]) / abs(grad_v[v]))
+    assert max(errs) < 1e-4, max(errs)
+
+
+def test_random_direction_derivative_128(lib):
+    """At 128^3: grad . d of omega_1 + ... + omega_5 for a dense random
+    direction d (uniform in [0.5, 1.5] at every voxel and component of eps)
+    against a central difference of eigensolves at eps +- h d, to 1e-6
+    relative.  Signed normal entries would cancel the gradient down to ~1e-6
+    (measured), below what solves accurate to ~1e-12 can difference at any
+    admissible step; with positive entries grad . d ~ 0.5 and h = 1e-4 puts
+    both the solvers' noise (~1e-11 / 2h) and the O(h^2) truncation near
+    1e-7 relative."""
+    w = wl.workload("field128")
+    g, k, med = w["grid"], w["kdota"], w["medium"]
+    opts = dict(precision="mixed", cg_tol=1e-12, eig_tol=1e-12)
+    ctx = lib.Context(g, k, med, **opts)
+    omega, Y, _ = ctx.eigs(6)
+    assert omega[4] < omega[5] * (1 - 1e-6)
+    d_eps, _ = ctx.eig_grad(Y[:5].contiguous(), np.ones(5))
+    ctx.close()
+    d = np.random.default_rng(128).uniform(0.5, 1.5, size=med.eps.shape)
+    an = float((d_eps.cpu().numpy() * d).sum())
+    h = 1e-4
+    f = []
+    for sgn in (1, -1):
+        m2 = wl.Medium(med.grid, med.kind, med.eps + sgn * h * d, med.gamma, med.mu, med.axes)
+        c2 = lib.Context(g, k, m2, **opts)
+        om2, _, _ = c2.eigs(6, vectors=False)
+        c2.close()
+        f.append(float(om2[:5].sum()))
+    fd = (f[0] - f[1]) / (2 * h)
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
