@@ -81,6 +81,8 @@ def parse():
                    help="skip the leg for media outside the Assumption (NFSEP at 8^3, shift-and-invert Arnoldi)")
     p.add_argument("--skip-fields", action="store_true",
                    help="skip the eigenvector-fields leg (E, H of the headline eigenpairs and their GEP residuals)")
+    p.add_argument("--cufft", action="store_true",
+                   help="with --matvec-only: also time cuFFT (torch.fft) on the product's twelve transforms")
     p.add_argument("--skip-paper-ncv", action="store_true",
                    help="skip the headline solve with the paper's basis size ncv = 3 nev")
     p.add_argument("--skip-sphere64", action="store_true", help="skip the 64^3 FP64 sphere leg (config 2)")
@@ -485,6 +487,35 @@ def nfsep_leg(nfs, wl, torch):
             "products_per_s": int(info.gmres_iterations) / dt}
 
 
+def cufft_comparison(torch, dev, grid, flush, stream, product_ms):
+    """Context for the product's time: the twelve 3-D FFTs of one A_r product
+    (six inverse, six forward, complex64) done by cuFFT through torch.fft on
+    the six field arrays alone, L2 flushed before each, against the whole
+    product (FFTs, spectral assembly, material and projections)."""
+    n1, n2, n3 = grid
+    x = torch.randn(6, n3, n2, n1, dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        torch.fft.ifftn(x, dim=(1, 2, 3))
+        torch.fft.fftn(x, dim=(1, 2, 3))
+    out = {}
+    for name, fn in (("ifftn_x6_ms", lambda: torch.fft.ifftn(x, dim=(1, 2, 3))),
+                     ("fftn_x6_ms", lambda: torch.fft.fftn(x, dim=(1, 2, 3)))):
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[name] = statistics.median(ts)
+    out["cufft_12_transforms_ms"] = out["ifftn_x6_ms"] + out["fftn_x6_ms"]
+    out["product_c64_ms"] = product_ms
+    out["product_vs_cufft_transforms"] = out["cufft_12_transforms_ms"] / product_ms
+    return out
+
+
 def sphere64_leg(nfs, wl, torch, np):
     """sphere64 (config 2): the 64^3 chiral sphere of seeded radius and
     chirality, the 20 smallest positive omega on the plain FP64 path, against
@@ -603,9 +634,11 @@ def run_ours(args):
             "pass_GBps_c64": [b / (t / 1e3) / 1e9 for b, t in zip(bpp, pass64)]}
     if args.matvec_only:
         if rank == 0:
-            print(json.dumps({"metric": "A_r products/s at 96^3 (pseudo96)", "mode": "matvec-only",
-                              "matvecs_per_s": {"c64": 1000.0 / mv64_ms, "c128": 1000.0 / mv128_ms},
-                              "roofline": roof}), flush=True)
+            line = {"metric": "A_r products/s at 96^3 (pseudo96)", "mode": "matvec-only",
+                    "matvecs_per_s": {"c64": 1000.0 / mv64_ms, "c128": 1000.0 / mv128_ms}, "roofline": roof}
+            if args.cufft:
+                line["cufft_comparison"] = cufft_comparison(torch, dev, grid, flush, stream, mv64_ms)
+            print(json.dumps(line), flush=True)
         ctx.close()
         return 0
 
