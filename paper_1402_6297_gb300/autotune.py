@@ -11,7 +11,7 @@ complex128 product, and improves the settings one knob at a time
 (coordinate descent from the current defaults).  The result is written to
 csrc/tuning.h, which every kernel header includes; rebuild afterwards.
 
-  python -m paper_1402_6297_gb300.autotune --sizes 48,64,96 [--rounds 1]
+  python -m paper_1402_6297_gb300.autotune --sizes 48,64,96 [--rounds 1] [--knobs A,B]
 
 Needs a GPU.  Each variant is a full build (a minute or two on 16 cores).
 """
@@ -44,11 +44,15 @@ KNOBS = {
     "NFS_C64_PAIRS": [0, 1],
     "NFS_PASS1_FUSED_LOAD": [0, 1],
     "NFS_SPLIT_C64": [0, 1],
+    "NFS_PK": [1, 0],
+    "NFS_PK1_FUSED": [0, 1],
+    "NFS_PK3": [0, 1],
 }
 MIN_GAIN = 0.03  # relative improvement a knob change must show to be taken
 
 # knobs that only matter for some sizes
-KNOB_SIZES = {"NFS_N1_32": {32}, "NFS_N1_48": {48}, "NFS_N1_64": {64}, "NFS_N1_96": {96}, "NFS_N1_128": {128}}
+KNOB_SIZES = {"NFS_N1_32": {32}, "NFS_N1_48": {48}, "NFS_N1_64": {64}, "NFS_N1_96": {96}, "NFS_N1_128": {128},
+              "NFS_PK1_FUSED": {96}, "NFS_PK3": {96}}
 
 
 def time_variant(lib, size, reps=60):
@@ -129,7 +133,12 @@ def main():
     ap.add_argument("--sizes", default="48,64,96")
     ap.add_argument("--rounds", type=int, default=1)
     ap.add_argument("--jobs", type=int, default=4, help="variants built in parallel")
+    ap.add_argument("--knobs", default="", help="comma-separated subset of the knobs to tune (default: all)")
     args = ap.parse_args()
+    tuned = [k for k in args.knobs.split(",") if k] or list(KNOBS)
+    unknown = [k for k in tuned if k not in KNOBS]
+    if unknown:
+        raise SystemExit(f"unknown knobs: {unknown}")
     sizes = [int(x) for x in args.sizes.split(",")]
     best = {k: v[0] for k, v in KNOBS.items()}
     cache = {}
@@ -137,7 +146,8 @@ def main():
         base = score(best, sizes, workdir, cache)
         print(json.dumps({"defaults": best, "score": base}), flush=True)
         for _ in range(args.rounds):
-            for knob, values in KNOBS.items():
+            for knob in tuned:
+                values = KNOBS[knob]
                 if knob in KNOB_SIZES and not (KNOB_SIZES[knob] & set(sizes)):
                     continue
                 cands = [dict(best, **{knob: v}) for v in values if v != best[knob]]

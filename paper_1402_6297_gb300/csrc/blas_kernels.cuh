@@ -381,41 +381,6 @@ __global__ void k_multi_axpy(double2* __restrict__ w, double2* __restrict__ Mw, 
   }
 }
 
-// In-place basis rotation V_p[:, 0:k] = V_p[:, 0:m] Y_p (Y_p real, m x k,
-// column-major, at Y + p * m * k); grid (blocks, P).  Each block stages TE
-// elements of all m vectors in shared memory first.
-template <int TE>
-__global__ void k_rotate_basis(double2* __restrict__ V, long long vstride, int m, const double* __restrict__ Y, int k,
-                               long long N, const int* __restrict__ active) {
-  const int p = blockIdx.y;
-  if (active && !active[p]) return;
-  V += (long long)p * vstride;
-  Y += (long long)p * m * k;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* tile = reinterpret_cast<double2*>(smem_raw);  // [m][TE]
-  for (long long base = (long long)blockIdx.x * TE; base < N; base += (long long)gridDim.x * TE) {
-    for (int idx = threadIdx.x; idx < m * TE; idx += blockDim.x) {
-      const int j = idx / TE, t = idx % TE;
-      const long long i = base + t;
-      tile[idx] = i < N ? V[(long long)j * N + i] : make_double2(0.0, 0.0);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < k * TE; idx += blockDim.x) {
-      const int col = idx / TE, t = idx % TE;
-      const long long i = base + t;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int j = 0; j < m; ++j) {
-        const double y = Y[(long long)col * m + j];
-        const double2 v = tile[j * TE + t];
-        acc.x += y * v.x;
-        acc.y += y * v.y;
-      }
-      if (i < N) V[(long long)col * N + i] = acc;
-    }
-    __syncthreads();
-  }
-}
-
 // Re-orthogonalisation through the shadows: w_p -= sum_j d_pj V32_pj and
 // Mw_p -= sum_j d_pj MV32_pj for j < m, with d (layout of k_dots_finish, on the
 // device) exact A_r inner products.  It runs only when the loss of
@@ -491,6 +456,76 @@ struct DSAccX2 {
 
 __device__ __forceinline__ float2 split_lo(double2 v, float2 hi) {
   return make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+}
+
+// In-place basis rotation V_p[:, 0:k] = V_p[:, 0:m] Y_p (Y_p real, m x k,
+// column-major), in double-single arithmetic on the FP32 units: Y is given
+// as float pairs Yhl[p m k + col m + j] = (hi, lo) with hi + lo = Y to ~1e-15,
+// each block stages TE elements of all m vectors in shared memory split the
+// same way, and every product hi x hi is formed exactly (TwoProduct) and
+// summed exactly (TwoSum) with the cross terms and rounding errors in an
+// ordinary FP32 sum: ~1e-14 of sum |terms|, at a small fraction of the cost
+// of FP64 arithmetic (m k FP64 FMAs per element otherwise).  A thread forms
+// CPT columns of one element.  Grid (blocks, P); problems with a zero flag
+// are skipped.
+template <int TE, int CPT>
+__global__ void __launch_bounds__(256)
+k_rotate_basis(double2* __restrict__ V, long long vstride, int m, const float2* __restrict__ Yhl, int k, long long N,
+               const int* __restrict__ active) {
+  const int p = blockIdx.y;
+  if (active && !active[p]) return;
+  V += (long long)p * vstride;
+  Yhl += (long long)p * m * k;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* tile = reinterpret_cast<float4*>(smem_raw);  // [m][TE]: (re hi, im hi, re lo, im lo)
+  const int groups = (k + CPT - 1) / CPT;
+  for (long long base = (long long)blockIdx.x * TE; base < N; base += (long long)gridDim.x * TE) {
+    for (int idx = threadIdx.x; idx < m * TE; idx += blockDim.x) {
+      const int j = idx / TE, t = idx % TE;
+      const long long i = base + t;
+      const double2 v = i < N ? V[(long long)j * N + i] : make_double2(0.0, 0.0);
+      const float2 h = make_float2((float)v.x, (float)v.y);
+      const float2 l = split_lo(v, h);
+      tile[idx] = make_float4(h.x, h.y, l.x, l.y);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < groups * TE; idx += blockDim.x) {
+      const int g = idx / TE, t = idx % TE;
+      const long long i = base + t;
+      DSAccX2 acc[CPT];
+      float2 small[CPT];
+      const float2* yc[CPT];
+#pragma unroll
+      for (int q = 0; q < CPT; ++q) {
+        small[q] = make_float2(0.f, 0.f);
+        yc[q] = Yhl + (long long)min(g * CPT + q, k - 1) * m;  // columns past k: computed, not stored
+      }
+      for (int j = 0; j < m; ++j) {
+        const float4 v = tile[j * TE + t];
+        const float2 vh = make_float2(v.x, v.y), vl = make_float2(v.z, v.w);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const float2 y = __ldg(yc[q] + j);
+          const float2 yh = make_float2(y.x, y.x), yl = make_float2(y.y, y.y);
+          float2 pr, e;
+          two_prod_x2(yh, vh, pr, e);
+          acc[q].add(pr);
+          small[q] = add_x2(small[q], fma_x2(yh, vl, fma_x2(yl, vh, e)));
+        }
+      }
+      if (i < N) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const int col = g * CPT + q;
+          if (col < k)
+            V[(long long)col * N + i] =
+                make_double2((double)acc[q].hi.x + ((double)acc[q].lo.x + (double)small[q].x),
+                             (double)acc[q].hi.y + ((double)acc[q].lo.y + (double)small[q].y));
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // out[(p * m + j) * 2 + {0,1}] = sum over the nb block partials of k_exact_dots; grid (m, P)

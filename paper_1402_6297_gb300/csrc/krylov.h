@@ -5,7 +5,10 @@
 // shift (shift-and-invert Arnoldi, Section 4).  The drivers own the small
 // projected matrices; every operation on the long vectors goes through a
 // KrylovOps object, so the same driver runs on device vectors (the library)
-// or on host vectors (the CPU tests).
+// or on host vectors (the CPU tests).  The library's inner GMRES solves run
+// the same iteration in a device-resident form (nfsep.h: the projected
+// problem stays in device memory, no host round trip per step); gmres()
+// below is its host statement, exercised on host operators by the CPU tests.
 #pragma once
 #include <complex>
 #include <vector>

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <chrono>
 #include <cmath>
 #include <cstdint>
@@ -41,6 +42,17 @@ using nfs::kRedThreads;
 namespace {
 struct GraphEntry {
   const void* key[5];
+  cudaGraphExec_t exec;
+};
+// A batch of GMRES steps as a replayable graph: steps j0 .. j0 + nsteps - 1
+// of a cycle of length m, for one shift and stopping threshold.
+struct GmresGraph {
+  int j0, nsteps, m;
+  const void* V;
+  const void* w;
+  const void* scratch;
+  double sigma_re, sigma_im, tolb;
+  long long kernels;  // kernel launches one replay makes
   cudaGraphExec_t exec;
 };
 }  // namespace
@@ -112,6 +124,7 @@ struct nfs_ctx {
   int ncv_set = 0;       // basis size chosen by a batch for this context (0: own default)
   size_t dY_len = 0;
   std::vector<GraphEntry> graphs;
+  std::vector<GmresGraph> gm_graphs;  // NFSEP inner-solve step batches
   long long bytes = 0;
   long long mv32 = 0, mv64 = 0;
   long long launches = 0;  // kernels this context has launched (graph nodes included)
@@ -684,6 +697,8 @@ int ensure_basis(nfs_ctx* c, int m) {
 // V_p[0:k] = V_p[0:m] Y_p for every problem flagged in d_active (Y: P blocks
 // of m x k, column-major); base is V or MV.
 int rotate(nfs_ctx* c, double2* base, int m, const std::vector<double>& Y, int k, const int* d_active) {
+  // Y as (hi, lo) float pairs (the kernel works in double-single); one float
+  // pair has the size of one double, so dY holds them
   const size_t need = (size_t)c->P * m * k;
   if (c->dY_len < need) {
     if (c->dY) cudaFree(c->dY);
@@ -691,15 +706,36 @@ int rotate(nfs_ctx* c, double2* base, int m, const std::vector<double>& Y, int k
     TRY(dalloc(c, &c->dY, need));
     c->dY_len = need;
   }
-  CK(cudaMemcpyAsync(c->dY, Y.data(), need * sizeof(double), cudaMemcpyHostToDevice, c->work));
-  constexpr int TE = 32;
-  const size_t smem = (size_t)m * TE * sizeof(double2);
-  CK(cudaFuncSetAttribute(nfs::k_rotate_basis<TE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  nfs::k_rotate_basis<TE><<<dim3(grid_blocks((c->N + TE - 1) / TE, 1), c->P), 256, smem, c->work>>>(
-      base, (long long)c->vcap * c->N, m, c->dY, k, c->N, d_active);
-  CK(cudaGetLastError());
+  std::vector<float> yhl(2 * need);
+  for (size_t i = 0; i < need; ++i) {
+    const float h = (float)Y[i];
+    yhl[2 * i] = h;
+    yhl[2 * i + 1] = (float)(Y[i] - (double)h);
+  }
+  CK(cudaMemcpyAsync(c->dY, yhl.data(), need * sizeof(double), cudaMemcpyHostToDevice, c->work));
+  // a tile of TE elements of all m vectors in shared memory: 32 while that
+  // fits in 200 KB, else narrower
+  constexpr int CPT = 4;
+  const float2* yhl_d = reinterpret_cast<const float2*>(c->dY);
+  auto launch = [&](auto te) -> cudaError_t {
+    constexpr int TE = decltype(te)::value;
+    const size_t smem = (size_t)m * TE * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(nfs::k_rotate_basis<TE, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    nfs::k_rotate_basis<TE, CPT><<<dim3(grid_blocks((c->N + TE - 1) / TE, 1), c->P), 256, smem, c->work>>>(
+        base, (long long)c->vcap * c->N, m, yhl_d, k, c->N, d_active);
+    return cudaGetLastError();
+  };
+  const size_t row = (size_t)m * sizeof(float4);
+  if (row * 32 <= 200 * 1024)
+    CK(launch(std::integral_constant<int, 32>{}));
+  else if (row * 16 <= 200 * 1024)
+    CK(launch(std::integral_constant<int, 16>{}));
+  else
+    CK(launch(std::integral_constant<int, 8>{}));
   c->launches += 1;
-  CK(cudaStreamSynchronize(c->work));  // Y's host buffer may be released next
+  CK(cudaStreamSynchronize(c->work));  // the host copy of Y is released next
   return NFS_OK;
 }
 
@@ -1303,6 +1339,7 @@ int join_caller(nfs_ctx* c) {
 void free_ctx(nfs_ctx* c) {
   if (!c) return;
   for (GraphEntry& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (GmresGraph& g : c->gm_graphs) cudaGraphExecDestroy(g.exec);
   void* ptrs[] = {c->lam64, c->lam32, c->tw64[0], c->tw64[1], c->tw64[2], c->tw32[0], c->tw32[1], c->tw32[2],
                   c->mat64, c->mat32, c->basis64, c->bloch64, c->lamdf, c->twdf[0], c->twdf[1], c->twdf[2], c->matdf,
                   c->basisdf, c->fld, c->x64, c->r64, c->p64, c->Ap64, c->t64, c->t64b, c->x32, c->r32,
@@ -1932,7 +1969,7 @@ struct DevBasis : virtual nfs::host::KrylovOps {
   double2* w;
   long long N;
   cudaStream_t s;
-  DevBasis(nfs_ctx* ctx, double2* basis, double2* work) : c(ctx), V(basis), w(work), N(ctx->N), s(ctx->stream) {}
+  DevBasis(nfs_ctx* ctx, double2* basis, double2* work) : c(ctx), V(basis), w(work), N(ctx->N), s(ctx->work) {}
   int put_coef(const std::vector<cplxd>& cf, double* dst) {
     for (size_t i = 0; i < cf.size(); ++i) {
       c->hscratch[2 * i] = cf[i].real();
@@ -2013,49 +2050,169 @@ struct DevBasis : virtual nfs::host::KrylovOps {
   }
 };
 
-// GMRES on (M - sigma I) x = b
-struct DevGmres : DevBasis, nfs::host::GmresOps {
-  const double2* b = nullptr;
-  double2* x;
-  double2 sigma;
-  DevGmres(nfs_ctx* ctx, double2* basis, double2* work, double2* xv, double2 sg)
-      : DevBasis(ctx, basis, work), x(xv), sigma(sg) {}
-  int apply(int j) override { return nfsep_apply(c, s, V + (long long)j * N, w, V + (long long)j * N, sigma); }
-  int residual() override {
-    TRY(nfsep_apply(c, s, x, w, x, sigma));
-    nfs::k_sub<double2><<<grid_blocks(N, 256), 256, 0, s>>>(b, w, w, N);
-    CK(cudaGetLastError());
-    c->launches += 1;
-    return NFS_OK;
+// Scratch of the device GMRES (offsets in doubles into dscratch): the two
+// Gram-Schmidt passes' partials, the norm partials, the GmresDev state.
+constexpr size_t kGsPartLen = (size_t)64 * nfs::kGmresMax * 2;
+constexpr size_t kGsNrmLen = 152 * 16 + 128;
+constexpr size_t kGsStateOff = 2 * kGsPartLen + kGsNrmLen;
+constexpr size_t kGsScratchLen = kGsStateOff + (sizeof(nfs::GmresDev) + 15) / 8;
+static_assert(kGsStateOff % 2 == 0, "the GMRES state must be 16-byte aligned");
+// steps enqueued between two host reads of the GMRES state
+constexpr int kGmresBatch = 10;
+
+// Steps j0 .. j0 + nsteps - 1 of a GMRES cycle of length m on stream s:
+// w = (M - sigma I) V_j, two classical Gram-Schmidt passes, the Givens
+// update of the projected problem, V_{j+1} = w / h_{j+1,j}.
+int enqueue_gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* w, int m, int j0, int nsteps,
+                        double tolb) {
+  const long long N = c->N;
+  double* part1 = c->dscratch;
+  double* part2 = c->dscratch + kGsPartLen;
+  double* nrm = c->dscratch + 2 * kGsPartLen;
+  auto* st = reinterpret_cast<nfs::GmresDev*>(c->dscratch + kGsStateOff);
+  const int S = nfs::gs_chunks(N), nb = nfs::gs_norm_blocks(N);
+  for (int j = j0; j < j0 + nsteps; ++j) {
+    const double2* vj = V + (long long)j * N;
+    TRY(nfsep_apply(c, s, vj, w, vj, sigma));
+    CK(nfs::gs_dots(V, j + 1, w, N, part1, s));
+    CK(nfs::gs_axpy(w, V, N, j + 1, part1, nullptr, s));
+    CK(nfs::gs_dots(V, j + 1, w, N, part2, s));
+    CK(nfs::gs_axpy(w, V, N, j + 1, part2, nrm, s));
+    CK(nfs::gmres_step(j, part1, part2, S, nrm, nb, st, tolb, s));
+    c->launches += 5;
+    if (j + 1 < m) {
+      CK(nfs::gmres_store(w, V + (long long)(j + 1) * N, st, N, s));
+      c->launches += 1;
+    }
   }
-  int update(int m, const std::vector<cplxd>& y) override {
-    double* dc = c->dscratch;
-    TRY(put_coef(y, dc));
-    CK(nfs::zaxpy_basis(x, V, N, dc, m, -1.0, s));
-    c->launches += 1;
+  return NFS_OK;
+}
+
+// The same steps as a CUDA graph, captured on first use per (j0, nsteps, m,
+// buffers, shift, threshold) and replayed on later cycles and solves: one
+// launch instead of about eleven per step.  s must be the context's work
+// stream (graph capture is not possible on the legacy default stream).
+#ifndef NFS_GMRES_GRAPH
+#define NFS_GMRES_GRAPH 1
+#endif
+int gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* w, int m, int j0, int nsteps,
+                double tolb) {
+  if (!NFS_GMRES_GRAPH) return enqueue_gmres_steps(c, s, sigma, V, w, m, j0, nsteps, tolb);
+  // one set of batches is kept: a new shift, threshold or buffer replaces it
+  if (!c->gm_graphs.empty()) {
+    const GmresGraph& f = c->gm_graphs.front();
+    if (f.m != m || f.V != V || f.w != w || f.scratch != c->dscratch || f.sigma_re != sigma.x ||
+        f.sigma_im != sigma.y || f.tolb != tolb) {
+      for (GmresGraph& g : c->gm_graphs) cudaGraphExecDestroy(g.exec);
+      c->gm_graphs.clear();
+    }
+  }
+  for (const GmresGraph& g : c->gm_graphs)
+    if (g.j0 == j0 && g.nsteps == nsteps) {
+      CK(cudaGraphLaunch(g.exec, s));
+      c->launches += g.kernels;
+      return NFS_OK;
+    }
+  const long long l0 = c->launches;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int rc = enqueue_gmres_steps(c, s, sigma, V, w, m, j0, nsteps, tolb);
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  const long long kernels = c->launches - l0;
+  c->launches = l0;
+  if (rc != NFS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture (gmres)");
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (gmres)");
+  c->gm_graphs.push_back(GmresGraph{j0, nsteps, m, V, w, c->dscratch, sigma.x, sigma.y, tolb, kernels, exec});
+  CK(cudaGraphLaunch(exec, s));
+  c->launches += kernels;
+  return NFS_OK;
+}
+
+// Restarted GMRES(m) on (M - sigma I) x = b (x holds the start iterate):
+// the iteration of nfs::host::gmres with the projected problem on the device
+// (nfsep.h), V (m + 1 vectors) and w as workspace.  A cycle is enqueued
+// kGmresBatch steps at a time; between batches the host reads the state's
+// header (done, k) once.  Steps enqueued after convergence inside a batch
+// are no-ops on the state and store zeros; they are counted as iterations.
+int dev_gmres(nfs_ctx* c, const double2* b, double2* x, double2 sigma, double2* V, double2* w, int m, double tol,
+              double bnorm, int maxit, nfs::host::GmresResult& out) {
+  out = nfs::host::GmresResult{};
+  if (m < 1 || m > nfs::kGmresMax || !(tol > 0.0)) return NFS_EINVAL;
+  if (!(bnorm > 0.0)) return NFS_OK;
+  cudaStream_t s = c->work;
+  const long long N = c->N;
+  double* nrm = c->dscratch + 2 * kGsPartLen;
+  auto* st = reinterpret_cast<nfs::GmresDev*>(c->dscratch + kGsStateOff);
+  const int nb = nfs::gs_norm_blocks(N);
+  const double tolb = tol * bnorm;
+  nfs::GmresHeader hdr;
+  auto read_header = [&]() -> int {
+    CK(cudaMemcpyAsync(c->hscratch, &st->h, sizeof(hdr), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    std::memcpy(&hdr, c->hscratch, sizeof(hdr));
     return NFS_OK;
+  };
+  for (;;) {
+    // r = b - (M - sigma I) x; V_0 = r / ||r||
+    TRY(nfsep_apply(c, s, x, w, x, sigma));
+    CK(nfs::gmres_residual(b, w, N, nrm, s));
+    CK(nfs::gmres_start(nrm, nb, st, tolb, s));
+    CK(nfs::gmres_store(w, V, st, N, s));
+    c->launches += 3;
+    TRY(read_header());
+    out.relres = hdr.beta / bnorm;
+    if (hdr.done) return NFS_OK;
+    if (out.iterations >= maxit) {
+      out.status = NFS_ENOCONV;
+      return NFS_OK;
+    }
+    int j = 0;
+    while (j < m && out.iterations < maxit) {
+      const int steps = std::min({kGmresBatch, m - j, maxit - out.iterations});
+      TRY(gmres_steps(c, s, sigma, V, w, m, j, steps, tolb));
+      j += steps;
+      out.iterations += steps;
+      TRY(read_header());
+      if (hdr.done) break;
+    }
+    // y = R^{-1} g over the cycle's k columns, x += V y
+    CK(nfs::gmres_solve(st, s));
+    CK(nfs::zaxpy_basis(x, V, N, reinterpret_cast<const double*>(st->y), hdr.k, -1.0, s));
+    c->launches += 2;
+    ++out.restarts;
+    TRY(read_header());
+    if (hdr.status != 0) return NFS_EBREAKDOWN;  // a zero pivot in the back substitution
   }
-};
+}
 
 // Arnoldi on (M - sigma I)^{-1}: each application one GMRES solve
 struct DevShiftInvert : DevBasis {
-  DevGmres& g;
+  double2* gV;  // GMRES basis
+  double2* gw;  // GMRES work vector
+  double2* gx;  // GMRES iterate
+  double2 sigma;
   int gm;
   double tol;
   int maxit;
   long long inner = 0;
-  DevShiftInvert(nfs_ctx* ctx, double2* basis, double2* work, DevGmres& gg, int m_inner, double t, int mi)
-      : DevBasis(ctx, basis, work), g(gg), gm(m_inner), tol(t), maxit(mi) {}
+  DevShiftInvert(nfs_ctx* ctx, double2* basis, double2* work, double2* gbasis, double2* gwork, double2* gxv,
+                 double2 sg, int m_inner, double t, int mi)
+      : DevBasis(ctx, basis, work), gV(gbasis), gw(gwork), gx(gxv), sigma(sg), gm(m_inner), tol(t), maxit(mi) {}
   int apply(int j) override {
-    g.b = V + (long long)j * N;
-    CK(cudaMemsetAsync(g.x, 0, N * sizeof(double2), s));
+    CK(cudaMemsetAsync(gx, 0, N * sizeof(double2), s));
     nfs::host::GmresResult r;
     // the Arnoldi vectors have unit norm
-    TRY(nfs::host::gmres(g, gm, tol, 1.0, maxit, r));
+    TRY(dev_gmres(c, V + (long long)j * N, gx, sigma, gV, gw, gm, tol, 1.0, maxit, r));
     inner += r.iterations;
     if (r.status != 0) return NFS_ENOCONV;
-    CK(cudaMemcpyAsync(w, g.x, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(w, gx, N * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     return NFS_OK;
   }
 };
@@ -2077,7 +2234,8 @@ int ensure_nfsep_bases(nfs_ctx* c, int m, int gm) {
     TRY(dalloc(c, &c->gv, (size_t)(gm + 1) * c->N));
     c->gv_cap = gm + 1;
   }
-  return ensure_scratch(c, (size_t)kRedBlocks * 2 * (std::max(m, gm) + 2) + 4 * (size_t)(std::max(m, gm) + 2) + 64);
+  return ensure_scratch(c, std::max(kGsScratchLen, (size_t)kRedBlocks * 2 * (std::max(m, gm) + 2) +
+                                                        4 * (size_t)(std::max(m, gm) + 2) + 64));
 }
 
 }  // namespace
@@ -2151,12 +2309,14 @@ extern "C" int nfs_nfsep_eigs(nfs_ctx* c, int nev, const double sigma[2], double
   TRY(ensure_nfsep_bases(c, m, gm));
   const double2 sg = make_double2(sigma[0], sigma[1]);
   const long long launches_0 = c->launches;
+  // everything below runs on the work stream (the GMRES step batches are
+  // captured as graphs), ordered after the caller's stream
+  TRY(join_caller(c));
   // start vector
-  nfs::k_random_fill<<<grid_blocks(c->N, 256), 256, 0, c->stream>>>(c->zv, c->N, 0, 1, c->opt.seed);
+  nfs::k_random_fill<<<grid_blocks(c->N, 256), 256, 0, c->work>>>(c->zv, c->N, 0, 1, c->opt.seed);
   CK(cudaGetLastError());
   c->launches += 1;
-  DevGmres g(c, c->gv, c->r64, c->x64, sg);
-  DevShiftInvert op(c, c->zv, c->p64, g, gm, c->opt.cg_tol, c->opt.cg_maxit);
+  DevShiftInvert op(c, c->zv, c->p64, c->gv, c->r64, c->x64, sg, gm, c->opt.cg_tol, c->opt.cg_maxit);
   nfs::host::ArnoldiResult r;
   const int rc = nfs::host::krylov_schur(op, nev, m, c->opt.eig_tol, c->opt.max_restarts, r);
   if (rc != NFS_OK) {
@@ -2176,8 +2336,8 @@ extern "C" int nfs_nfsep_eigs(nfs_ctx* c, int nev, const double sigma[2], double
     omega[2 * e] = lam.real();
     omega[2 * e + 1] = lam.imag();
   }
-  if (Y) CK(cudaMemcpyAsync(Y, c->zv, (size_t)nev * c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  if (Y) CK(cudaMemcpyAsync(Y, c->zv, (size_t)nev * c->N * sizeof(double2), cudaMemcpyDeviceToDevice, c->work));
+  CK(cudaStreamSynchronize(c->work));
   if (info) {
     info->arnoldi_steps = r.steps;
     info->restarts = r.restarts;

@@ -40,4 +40,56 @@ cudaError_t zscale_copy(const double2* src, double2* dst, double scale, long lon
 // V_i <- sum_{r<m} V_r Y[r k + i], i < k, in place (Y device interleaved complex)
 cudaError_t zrotate(double2* V, int m, const double* Y, int k, long long N, cudaStream_t s);
 
+// Restarted GMRES with the projected problem on the device (the library's
+// inner solver for (M - sigma I) z = b): the Gram-Schmidt coefficients, the
+// Hessenberg matrix, its Givens rotations and the back substitution stay in
+// device memory, so a GMRES cycle is enqueued without a host round trip per
+// step.  The iteration is that of nfs::host::gmres (krylov.h): two classical
+// Gram-Schmidt passes per step, stop at |g_{j+1}| <= tol ||b|| (the residual
+// norm of the small least-squares problem) or h_{j+1,j} = 0.
+constexpr int kGmresMax = 128;  // largest restart length
+struct GmresHeader {  // what the host reads between batches of steps
+  int done;       // 1 once converged or h_{j+1,j} = 0; the cycle's later steps are no-ops
+  int k;          // columns of the current cycle
+  int status;     // 0, or -7 if the back substitution met a zero pivot
+  int pad;
+  double inv_h;   // scale of the vector stored next: 1 / h_{j+1,j}, 1 / beta, 0 once done
+  double beta;    // ||b - Op x|| at the start of the cycle
+  double resid;   // |g_k|: the cycle's estimate of ||b - Op x||
+  double pad2;
+};
+struct GmresDev {
+  GmresHeader h;
+  double cs[kGmresMax];
+  double2 sn[kGmresMax];
+  double2 g[kGmresMax + 1];
+  double2 y[kGmresMax];
+  double2 H[(kGmresMax + 1) * kGmresMax];  // H(i, j) at H[i * kGmresMax + j]
+};
+
+// Chunks (S) of the Gram-Schmidt dot products for vectors of length N, and
+// the blocks of gs_axpy / gmres_residual (the number of norm partials).
+int gs_chunks(long long N);
+int gs_norm_blocks(long long N);
+// part[(s m + j) 2 + {0, 1}] = chunk s's share of V_j^* w, j < m (m <= kGmresMax)
+cudaError_t gs_dots(const double2* V, int m, const double2* w, long long N, double* part, cudaStream_t s);
+// w -= sum_{j<m} c_j V_j with c_j = sum_s part[(s m + j)]; with nrm_part,
+// nrm_part[b] = block b's share of ||w||^2 after the update
+cudaError_t gs_axpy(double2* w, const double2* V, long long N, int m, const double* part, double* nrm_part,
+                    cudaStream_t s);
+// w = b - w and the partials of ||w||^2
+cudaError_t gmres_residual(const double2* b, double2* w, long long N, double* nrm_part, cudaStream_t s);
+// Start of a cycle: beta = ||w|| from nb partials, g = beta e_0, done if
+// beta <= tolb, inv_h = 1 / beta
+cudaError_t gmres_start(const double* nrm_part, int nb, GmresDev* st, double tolb, cudaStream_t s);
+// Step j: column j of H from the two passes' partials (S chunks each, over
+// j + 1 vectors) and h_{j+1,j} from nb norm partials; the earlier rotations,
+// a new one, g, k = j + 1, done and inv_h.  No-op once done.
+cudaError_t gmres_step(int j, const double* part1, const double* part2, int S, const double* nrm_part, int nb,
+                       GmresDev* st, double tolb, cudaStream_t s);
+// dst = inv_h * w
+cudaError_t gmres_store(const double2* w, double2* dst, const GmresDev* st, long long N, cudaStream_t s);
+// y = R^{-1} g over the k columns of the cycle
+cudaError_t gmres_solve(GmresDev* st, cudaStream_t s);
+
 }  // namespace nfs

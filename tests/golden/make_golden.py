@@ -122,9 +122,33 @@ tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s on on
 """, om)
 
 
+def nfsep_grid(n):
+    """The four eigenvalues nearest 2 + 0.1i of the null space free standard
+    problem of the nfsep8 sphere on an n^3 grid (oracle shift-and-invert
+    Arnoldi with GMRES), with the wall time recorded."""
+    g = (n, n, n)
+    med = wl.biisotropic_sphere(g, 0.25, 13.0 + 2.0j, 1.0, 0.5, 0.2)
+    t0 = time.time()
+    om, _ = nfsep.NFSEP(g, (0.1, 0.2, 0.3), med).eigs_near(2.0 + 0.1j, 4)
+    dt = time.time() - t0
+    with open(os.path.join(HERE, f"nfsep{n}_omega.txt"), "w") as f:
+        f.write(f"""# 4 eigenvalues nearest sigma = 2 + 0.1i of M y = omega y (eq. NFSEP_org; thm:nfep: the GEP's
+# nonzero eigenvalues) for a bi-isotropic sphere outside the Assumption: radius 0.25, inside
+# eps = 13 + 2i, gamma = 0.5, chi = 0.2, mu = 1; outside vacuum; grid {n}x{n}x{n}, k.a = (0.1, 0.2, 0.3)
+# oracle: FFT NFSEP operator, shift-and-invert Arnoldi with GMRES (oracle.nfsep.NFSEP.eigs_near), FP64;
+# {dt:.0f} s on the host
+# columns: re, im (nearest sigma first)
+""")
+        for w in om:
+            f.write(f"{w.real:.17e} {w.imag:.17e}\n")
+
+
 if __name__ == "__main__":
     if len(sys.argv) > 1:
         for name in sys.argv[1:]:
-            large(name)
+            if name.startswith("nfsep"):
+                nfsep_grid(int(name[5:]))
+            else:
+                large(name)
     else:
         main()
