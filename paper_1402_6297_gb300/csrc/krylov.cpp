@@ -53,12 +53,55 @@ int orthogonalise(KrylovOps& ops, int n, std::vector<cplxd>& h) {
 
 }  // namespace
 
+void GivensLS::reset(int m, double beta) {
+  m_ = m;
+  k_ = 0;
+  R_.assign((size_t)(m + 1) * m, cplxd(0.0));
+  g_.assign(m + 1, cplxd(0.0));
+  sn_.assign(m, cplxd(0.0));
+  cs_.assign(m, 0.0);
+  g_[0] = beta;
+}
+
+double GivensLS::add_column(const cplxd* col, double h) {
+  const int j = k_;
+  auto Rc = [&](int r, int cc) -> cplxd& { return R_[(size_t)r * m_ + cc]; };
+  for (int i = 0; i <= j; ++i) Rc(i, j) = col[i];
+  Rc(j + 1, j) = h;
+  for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+    const cplxd x = Rc(i, j), y = Rc(i + 1, j);
+    Rc(i, j) = cs_[i] * x + sn_[i] * y;
+    Rc(i + 1, j) = -std::conj(sn_[i]) * x + cs_[i] * y;
+  }
+  rotation(Rc(j, j), Rc(j + 1, j), cs_[j], sn_[j]);
+  const cplxd x = Rc(j, j), y = Rc(j + 1, j);
+  Rc(j, j) = cs_[j] * x + sn_[j] * y;
+  Rc(j + 1, j) = 0.0;
+  const cplxd gj = g_[j];
+  g_[j] = cs_[j] * gj;
+  g_[j + 1] = -std::conj(sn_[j]) * gj;
+  k_ = j + 1;
+  return std::abs(g_[j + 1]);
+}
+
+bool GivensLS::solve(std::vector<cplxd>& y) const {
+  y.assign(k_, cplxd(0.0));
+  for (int i = k_ - 1; i >= 0; --i) {
+    cplxd acc = g_[i];
+    for (int q = i + 1; q < k_; ++q) acc -= R_[(size_t)i * m_ + q] * y[q];
+    const cplxd d = R_[(size_t)i * m_ + i];
+    if (d == cplxd(0.0)) return false;
+    y[i] = acc / d;
+  }
+  return true;
+}
+
 int gmres(GmresOps& ops, int m, double tol, double bnorm, int maxit, GmresResult& out) {
   out = GmresResult{};
   if (m < 1 || !(tol > 0.0)) return -1;
   if (!(bnorm > 0.0)) return kOk;  // b = 0: x is left as it is
-  std::vector<cplxd> H((size_t)(m + 1) * m), g(m + 1), sn(m), col;
-  std::vector<double> cs(m);
+  GivensLS ls;
+  std::vector<cplxd> col;
   for (;;) {
     KRY_TRY(ops.residual());
     double beta = 0.0;
@@ -70,48 +113,22 @@ int gmres(GmresOps& ops, int m, double tol, double bnorm, int maxit, GmresResult
       return kOk;
     }
     KRY_TRY(ops.store(0, 1.0 / beta));
-    std::fill(H.begin(), H.end(), cplxd(0.0));
-    std::fill(g.begin(), g.end(), cplxd(0.0));
-    g[0] = beta;
-    int k = 0;
+    ls.reset(m, beta);
     for (int j = 0; j < m; ++j) {
       KRY_TRY(ops.apply(j));
       ++out.iterations;
       KRY_TRY(orthogonalise(ops, j + 1, col));
       double h = 0.0;
       KRY_TRY(ops.norm(h));
-      auto Hc = [&](int r, int cc) -> cplxd& { return H[(size_t)r * m + cc]; };
-      for (int i = 0; i <= j; ++i) Hc(i, j) = col[i];
-      Hc(j + 1, j) = h;
-      for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
-        const cplxd x = Hc(i, j), y = Hc(i + 1, j);
-        Hc(i, j) = cs[i] * x + sn[i] * y;
-        Hc(i + 1, j) = -std::conj(sn[i]) * x + cs[i] * y;
-      }
-      rotation(Hc(j, j), Hc(j + 1, j), cs[j], sn[j]);
-      {
-        const cplxd x = Hc(j, j), y = Hc(j + 1, j);
-        Hc(j, j) = cs[j] * x + sn[j] * y;
-        Hc(j + 1, j) = 0.0;
-        const cplxd gj = g[j];
-        g[j] = cs[j] * gj;
-        g[j + 1] = -std::conj(sn[j]) * gj;
-      }
-      k = j + 1;
-      const bool done = std::abs(g[j + 1]) <= tol * bnorm || out.iterations >= maxit || h == 0.0;
+      const double res = ls.add_column(col.data(), h);
+      const bool done = res <= tol * bnorm || out.iterations >= maxit || h == 0.0;
       if (!done && j + 1 < m) KRY_TRY(ops.store(j + 1, 1.0 / h));
       if (done) break;
     }
-    // y = R^{-1} g over the k columns, x += V y
-    std::vector<cplxd> y(k);
-    for (int i = k - 1; i >= 0; --i) {
-      cplxd acc = g[i];
-      for (int q = i + 1; q < k; ++q) acc -= H[(size_t)i * m + q] * y[q];
-      const cplxd d = H[(size_t)i * m + i];
-      if (d == cplxd(0.0)) return kBreakdown;
-      y[i] = acc / d;
-    }
-    KRY_TRY(ops.update(k, y));
+    // y = R^{-1} g over the cycle's columns, x += V y
+    std::vector<cplxd> y;
+    if (!ls.solve(y)) return kBreakdown;
+    KRY_TRY(ops.update(ls.columns(), y));
     ++out.restarts;
   }
 }

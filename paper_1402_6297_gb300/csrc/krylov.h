@@ -6,9 +6,10 @@
 // projected matrices; every operation on the long vectors goes through a
 // KrylovOps object, so the same driver runs on device vectors (the library)
 // or on host vectors (the CPU tests).  The library's inner GMRES solves run
-// the same iteration in a device-resident form (nfsep.h: the projected
-// problem stays in device memory, no host round trip per step); gmres()
-// below is its host statement, exercised on host operators by the CPU tests.
+// the same iteration with the Gram-Schmidt coefficients kept on the device
+// and the Hessenberg columns read in batches (nfsep.h), the least-squares
+// part through GivensLS below; gmres() is the host statement of that
+// iteration, exercised on host operators by the CPU tests.
 #pragma once
 #include <complex>
 #include <vector>
@@ -47,6 +48,25 @@ struct GmresResult {
   int restarts = 0;
   double relres = 0.0;  // final ||b - Op x|| / ||b||
   int status = 0;       // 0 or NFS_ENOCONV (-6)
+};
+
+// The small least-squares problem of a GMRES cycle, min ||beta e_0 - H y||
+// over the (j + 2) x (j + 1) upper Hessenberg H, kept factored by Givens
+// rotations G = [[c, s], [-conj(s), c]] as the columns arrive: after column j
+// the residual norm of the cycle's best iterate is |g_{j+1}|.
+class GivensLS {
+ public:
+  void reset(int m, double beta);
+  // column j of H: col[0..j], h = h_{j+1,j} >= 0; returns |g_{j+1}|
+  double add_column(const cplxd* col, double h);
+  int columns() const { return k_; }
+  // y = R^{-1} g over the columns so far; false on a zero pivot
+  bool solve(std::vector<cplxd>& y) const;
+
+ private:
+  int m_ = 0, k_ = 0;
+  std::vector<cplxd> R_, g_, sn_;  // R_ row-major (m + 1) x m
+  std::vector<double> cs_;
 };
 
 // Restarted GMRES(m) from the iterate the ops hold, modified Gram-Schmidt

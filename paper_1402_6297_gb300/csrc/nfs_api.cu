@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <new>
@@ -45,13 +46,13 @@ struct GraphEntry {
   cudaGraphExec_t exec;
 };
 // A batch of GMRES steps as a replayable graph: steps j0 .. j0 + nsteps - 1
-// of a cycle of length m, for one shift and stopping threshold.
+// of a cycle of length m, for one shift.
 struct GmresGraph {
   int j0, nsteps, m;
   const void* V;
   const void* w;
   const void* scratch;
-  double sigma_re, sigma_im, tolb;
+  double sigma_re, sigma_im;
   long long kernels;  // kernel launches one replay makes
   cudaGraphExec_t exec;
 };
@@ -2051,35 +2052,38 @@ struct DevBasis : virtual nfs::host::KrylovOps {
 };
 
 // Scratch of the device GMRES (offsets in doubles into dscratch): the two
-// Gram-Schmidt passes' partials, the norm partials, the GmresDev state.
+// Gram-Schmidt passes' partials, the norm partials, the least-squares
+// solution, the GmresDev state, then gs_axpy's partial sums.
 constexpr size_t kGsPartLen = (size_t)64 * nfs::kGmresMax * 2;
 constexpr size_t kGsNrmLen = 152 * 16 + 128;
-constexpr size_t kGsStateOff = 2 * kGsPartLen + kGsNrmLen;
-constexpr size_t kGsScratchLen = kGsStateOff + (sizeof(nfs::GmresDev) + 15) / 8;
-static_assert(kGsStateOff % 2 == 0, "the GMRES state must be 16-byte aligned");
-// steps enqueued between two host reads of the GMRES state
+constexpr size_t kGsYOff = 2 * kGsPartLen + kGsNrmLen;
+constexpr size_t kGsStateOff = kGsYOff + 2 * nfs::kGmresMax;
+constexpr size_t kGsTmpOff = kGsStateOff + (sizeof(nfs::GmresDev) + 15) / 16 * 2;
+static_assert(kGsYOff % 2 == 0 && kGsStateOff % 2 == 0 && kGsTmpOff % 2 == 0, "16-byte alignment");
+size_t gs_scratch_len(long long N) { return kGsTmpOff + 2 * (size_t)nfs::gs_axpy_tmp_len(N); }
+// steps enqueued between two host reads of the Hessenberg columns
 constexpr int kGmresBatch = 10;
 
 // Steps j0 .. j0 + nsteps - 1 of a GMRES cycle of length m on stream s:
-// w = (M - sigma I) V_j, two classical Gram-Schmidt passes, the Givens
-// update of the projected problem, V_{j+1} = w / h_{j+1,j}.
-int enqueue_gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* w, int m, int j0, int nsteps,
-                        double tolb) {
+// w = (M - sigma I) V_j, two classical Gram-Schmidt passes, column j of H,
+// V_{j+1} = w / h_{j+1,j}.
+int enqueue_gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* w, int m, int j0, int nsteps) {
   const long long N = c->N;
   double* part1 = c->dscratch;
   double* part2 = c->dscratch + kGsPartLen;
   double* nrm = c->dscratch + 2 * kGsPartLen;
   auto* st = reinterpret_cast<nfs::GmresDev*>(c->dscratch + kGsStateOff);
+  auto* tmp = reinterpret_cast<double2*>(c->dscratch + kGsTmpOff);
   const int S = nfs::gs_chunks(N), nb = nfs::gs_norm_blocks(N);
   for (int j = j0; j < j0 + nsteps; ++j) {
     const double2* vj = V + (long long)j * N;
     TRY(nfsep_apply(c, s, vj, w, vj, sigma));
     CK(nfs::gs_dots(V, j + 1, w, N, part1, s));
-    CK(nfs::gs_axpy(w, V, N, j + 1, part1, nullptr, s));
+    CK(nfs::gs_axpy(w, V, N, j + 1, part1, nullptr, tmp, s));
     CK(nfs::gs_dots(V, j + 1, w, N, part2, s));
-    CK(nfs::gs_axpy(w, V, N, j + 1, part2, nrm, s));
-    CK(nfs::gmres_step(j, part1, part2, S, nrm, nb, st, tolb, s));
-    c->launches += 5;
+    CK(nfs::gs_axpy(w, V, N, j + 1, part2, nrm, tmp, s));
+    CK(nfs::gmres_column(j, part1, part2, S, nrm, nb, st, s));
+    c->launches += 3 + 2 * nfs::gs_axpy_kernels(N);
     if (j + 1 < m) {
       CK(nfs::gmres_store(w, V + (long long)(j + 1) * N, st, N, s));
       c->launches += 1;
@@ -2089,20 +2093,19 @@ int enqueue_gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, d
 }
 
 // The same steps as a CUDA graph, captured on first use per (j0, nsteps, m,
-// buffers, shift, threshold) and replayed on later cycles and solves: one
-// launch instead of about eleven per step.  s must be the context's work
-// stream (graph capture is not possible on the legacy default stream).
+// buffers, shift) and replayed on later cycles and solves: one launch
+// instead of about a dozen per step.  s must be the context's work stream
+// (graph capture is not possible on the legacy default stream).
 #ifndef NFS_GMRES_GRAPH
 #define NFS_GMRES_GRAPH 1
 #endif
-int gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* w, int m, int j0, int nsteps,
-                double tolb) {
-  if (!NFS_GMRES_GRAPH) return enqueue_gmres_steps(c, s, sigma, V, w, m, j0, nsteps, tolb);
-  // one set of batches is kept: a new shift, threshold or buffer replaces it
+int gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* w, int m, int j0, int nsteps) {
+  if (!NFS_GMRES_GRAPH) return enqueue_gmres_steps(c, s, sigma, V, w, m, j0, nsteps);
+  // one set of batches is kept: a new shift or buffer replaces it
   if (!c->gm_graphs.empty()) {
     const GmresGraph& f = c->gm_graphs.front();
     if (f.m != m || f.V != V || f.w != w || f.scratch != c->dscratch || f.sigma_re != sigma.x ||
-        f.sigma_im != sigma.y || f.tolb != tolb) {
+        f.sigma_im != sigma.y) {
       for (GmresGraph& g : c->gm_graphs) cudaGraphExecDestroy(g.exec);
       c->gm_graphs.clear();
     }
@@ -2116,7 +2119,7 @@ int gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* 
   const long long l0 = c->launches;
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  const int rc = enqueue_gmres_steps(c, s, sigma, V, w, m, j0, nsteps, tolb);
+  const int rc = enqueue_gmres_steps(c, s, sigma, V, w, m, j0, nsteps);
   cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   const long long kernels = c->launches - l0;
   c->launches = l0;
@@ -2129,18 +2132,18 @@ int gmres_steps(nfs_ctx* c, cudaStream_t s, double2 sigma, double2* V, double2* 
   cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (gmres)");
-  c->gm_graphs.push_back(GmresGraph{j0, nsteps, m, V, w, c->dscratch, sigma.x, sigma.y, tolb, kernels, exec});
+  c->gm_graphs.push_back(GmresGraph{j0, nsteps, m, V, w, c->dscratch, sigma.x, sigma.y, kernels, exec});
   CK(cudaGraphLaunch(exec, s));
   c->launches += kernels;
   return NFS_OK;
 }
 
-// Restarted GMRES(m) on (M - sigma I) x = b (x holds the start iterate):
-// the iteration of nfs::host::gmres with the projected problem on the device
-// (nfsep.h), V (m + 1 vectors) and w as workspace.  A cycle is enqueued
-// kGmresBatch steps at a time; between batches the host reads the state's
-// header (done, k) once.  Steps enqueued after convergence inside a batch
-// are no-ops on the state and store zeros; they are counted as iterations.
+// Restarted GMRES(m) on (M - sigma I) x = b (x holds the start iterate), the
+// iteration of nfs::host::gmres: the long-vector work on the device (V, m + 1
+// vectors, and w as workspace), the least-squares problem on the host
+// (GivensLS) from the Hessenberg columns read once per batch of kGmresBatch
+// steps.  Steps enqueued after the one that converged are wasted work (the
+// cycle ends at the converged column); they are counted as iterations.
 int dev_gmres(nfs_ctx* c, const double2* b, double2* x, double2 sigma, double2* V, double2* w, int m, double tol,
               double bnorm, int maxit, nfs::host::GmresResult& out) {
   out = nfs::host::GmresResult{};
@@ -2149,46 +2152,65 @@ int dev_gmres(nfs_ctx* c, const double2* b, double2* x, double2 sigma, double2* 
   cudaStream_t s = c->work;
   const long long N = c->N;
   double* nrm = c->dscratch + 2 * kGsPartLen;
+  double* yd = c->dscratch + kGsYOff;
   auto* st = reinterpret_cast<nfs::GmresDev*>(c->dscratch + kGsStateOff);
   const int nb = nfs::gs_norm_blocks(N);
   const double tolb = tol * bnorm;
-  nfs::GmresHeader hdr;
-  auto read_header = [&]() -> int {
-    CK(cudaMemcpyAsync(c->hscratch, &st->h, sizeof(hdr), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    std::memcpy(&hdr, c->hscratch, sizeof(hdr));
-    return NFS_OK;
-  };
+  constexpr int kCol = nfs::kGmresMax + 1;
+  nfs::host::GivensLS ls;
+  std::vector<nfs::host::cplxd> col(kCol), y;
   for (;;) {
     // r = b - (M - sigma I) x; V_0 = r / ||r||
     TRY(nfsep_apply(c, s, x, w, x, sigma));
     CK(nfs::gmres_residual(b, w, N, nrm, s));
-    CK(nfs::gmres_start(nrm, nb, st, tolb, s));
-    CK(nfs::gmres_store(w, V, st, N, s));
-    c->launches += 3;
-    TRY(read_header());
-    out.relres = hdr.beta / bnorm;
-    if (hdr.done) return NFS_OK;
+    c->launches += 1;
+    CK(cudaMemcpyAsync(c->hscratch, nrm, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double bb = 0.0;
+    for (int i = 0; i < nb; ++i) bb += c->hscratch[i];
+    const double beta = std::sqrt(std::max(bb, 0.0));
+    out.relres = beta / bnorm;
+    if (beta <= tolb) return NFS_OK;
     if (out.iterations >= maxit) {
       out.status = NFS_ENOCONV;
       return NFS_OK;
     }
+    CK(cudaMemsetAsync(st, 0, 2 * sizeof(double2), s));  // done, inv_h
+    CK(nfs::zscale_copy(w, V, 1.0 / beta, N, s));
+    c->launches += 1;
+    ls.reset(m, beta);
     int j = 0;
-    while (j < m && out.iterations < maxit) {
+    bool done = false;
+    while (j < m && out.iterations < maxit && !done) {
       const int steps = std::min({kGmresBatch, m - j, maxit - out.iterations});
-      TRY(gmres_steps(c, s, sigma, V, w, m, j, steps, tolb));
+      TRY(gmres_steps(c, s, sigma, V, w, m, j, steps));
+      const auto* hc_dev = reinterpret_cast<const double2*>(reinterpret_cast<const char*>(st) +
+                                                             offsetof(nfs::GmresDev, Hc));
+      CK(cudaMemcpyAsync(c->hscratch, hc_dev + (size_t)j * kCol, (size_t)steps * kCol * sizeof(double2),
+                         cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int t = 0; t < steps && !done; ++t) {
+        const double* hc = c->hscratch + (size_t)t * kCol * 2;
+        const int jj = j + t;
+        for (int i = 0; i <= jj; ++i) col[i] = nfs::host::cplxd(hc[2 * i], hc[2 * i + 1]);
+        const double h = hc[2 * (jj + 1)];
+        const double res = ls.add_column(col.data(), h);
+        done = res <= tolb || h == 0.0;
+      }
       j += steps;
       out.iterations += steps;
-      TRY(read_header());
-      if (hdr.done) break;
     }
-    // y = R^{-1} g over the cycle's k columns, x += V y
-    CK(nfs::gmres_solve(st, s));
-    CK(nfs::zaxpy_basis(x, V, N, reinterpret_cast<const double*>(st->y), hdr.k, -1.0, s));
-    c->launches += 2;
+    // y = R^{-1} g over the cycle's columns, x += V y
+    if (!ls.solve(y)) return NFS_EBREAKDOWN;
+    for (size_t i = 0; i < y.size(); ++i) {
+      c->hscratch[2 * i] = y[i].real();
+      c->hscratch[2 * i + 1] = y[i].imag();
+    }
+    CK(cudaMemcpyAsync(yd, c->hscratch, y.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CK(nfs::zaxpy_basis(x, V, N, yd, ls.columns(), -1.0, s));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(s));  // the pinned staging buffer is reused next
     ++out.restarts;
-    TRY(read_header());
-    if (hdr.status != 0) return NFS_EBREAKDOWN;  // a zero pivot in the back substitution
   }
 }
 
@@ -2234,8 +2256,8 @@ int ensure_nfsep_bases(nfs_ctx* c, int m, int gm) {
     TRY(dalloc(c, &c->gv, (size_t)(gm + 1) * c->N));
     c->gv_cap = gm + 1;
   }
-  return ensure_scratch(c, std::max(kGsScratchLen, (size_t)kRedBlocks * 2 * (std::max(m, gm) + 2) +
-                                                        4 * (size_t)(std::max(m, gm) + 2) + 64));
+  return ensure_scratch(c, std::max(gs_scratch_len(c->N), (size_t)kRedBlocks * 2 * (std::max(m, gm) + 2) +
+                                                               4 * (size_t)(std::max(m, gm) + 2) + 64));
 }
 
 }  // namespace

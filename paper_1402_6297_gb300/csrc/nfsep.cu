@@ -255,6 +255,56 @@ k_gs_axpy(double2* __restrict__ w, const double2* __restrict__ V, long long N, i
   }
 }
 
+// Short vectors: grid (ceil(N / kGsThreads), chunks of kGsAxpyChunk basis
+// vectors); tmp[jc N + i] = sum over chunk jc of c_j V_j[i]
+constexpr int kGsAxpyChunk = 16;
+__global__ void __launch_bounds__(kGsThreads)
+k_gs_axpy_part(const double2* __restrict__ V, long long N, int m, const double* __restrict__ part, int S,
+               double2* __restrict__ tmp) {
+  __shared__ double2 cs[kGsAxpyChunk];
+  const int j0 = blockIdx.y * kGsAxpyChunk;
+  const int nj = min(kGsAxpyChunk, m - j0);
+  if (threadIdx.x < nj) {
+    double re = 0.0, im = 0.0;
+    for (int q = 0; q < S; ++q) {
+      re += part[((long long)q * m + j0 + threadIdx.x) * 2];
+      im += part[((long long)q * m + j0 + threadIdx.x) * 2 + 1];
+    }
+    cs[threadIdx.x] = make_double2(re, im);
+  }
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * kGsThreads + threadIdx.x;
+  if (i >= N) return;
+  double2 v[kGsAxpyChunk];
+#pragma unroll
+  for (int t = 0; t < kGsAxpyChunk; ++t) v[t] = t < nj ? V[(long long)(j0 + t) * N + i] : make_double2(0.0, 0.0);
+  double2 a0 = make_double2(0.0, 0.0), a1 = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int t = 0; t < kGsAxpyChunk; t += 2) {
+    if (t < nj) a0 = cadd(a0, cmul(cs[t], v[t]));
+    if (t + 1 < nj) a1 = cadd(a1, cmul(cs[t + 1], v[t + 1]));
+  }
+  tmp[(long long)blockIdx.y * N + i] = cadd(a0, a1);
+}
+
+// w -= sum over the JC partial sums in tmp, and the partials of ||w||^2
+__global__ void __launch_bounds__(kGsThreads)
+k_gs_axpy_sum(double2* __restrict__ w, long long N, const double2* __restrict__ tmp, int JC,
+              double* __restrict__ nrm_part) {
+  __shared__ double red[kGsThreads / 32];
+  double nr = 0.0;
+  for (long long i = (long long)blockIdx.x * kGsThreads + threadIdx.x; i < N; i += (long long)gridDim.x * kGsThreads) {
+    double2 a = w[i];
+    for (int jc = 0; jc < JC; ++jc) a = csub(a, tmp[(long long)jc * N + i]);
+    w[i] = a;
+    nr += cabs2(a);
+  }
+  if (nrm_part) {
+    nr = gs_block_sum(nr, red);
+    if (threadIdx.x == 0) nrm_part[blockIdx.x] = nr;
+  }
+}
+
 __global__ void __launch_bounds__(kGsThreads)
 k_gmres_residual(const double2* __restrict__ b, double2* __restrict__ w, long long N, double* __restrict__ nrm_part) {
   __shared__ double red[kGsThreads / 32];
@@ -275,38 +325,15 @@ __device__ __forceinline__ double gs_sum_partials(const double* part, int nb, do
 }
 
 __global__ void __launch_bounds__(kGsThreads)
-k_gmres_start(const double* __restrict__ nrm_part, int nb, GmresDev* st, double tolb) {
+k_gmres_column(int j, const double* __restrict__ part1, const double* __restrict__ part2, int S,
+               const double* __restrict__ nrm_part, int nb, GmresDev* st) {
   __shared__ double red[kGsThreads / 32];
-  const double beta = sqrt(fmax(gs_sum_partials(nrm_part, nb, red), 0.0));
-  if (threadIdx.x == 0) {
-    st->h.beta = beta;
-    st->h.resid = beta;
-    st->h.done = beta <= tolb ? 1 : 0;
-    st->h.k = 0;
-    st->h.status = 0;
-    st->g[0] = make_double2(beta, 0.0);
-    st->h.inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
-  }
-}
-
-// complex a / b for b != 0
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-  const double d = cabs2(b);
-  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
-
-__global__ void __launch_bounds__(kGsThreads)
-k_gmres_step(int j, const double* __restrict__ part1, const double* __restrict__ part2, int S,
-             const double* __restrict__ nrm_part, int nb, GmresDev* st, double tolb) {
-  __shared__ double red[kGsThreads / 32];
-  __shared__ double2 col[kGmresMax + 1];
-  __shared__ double csv[kGmresMax];
-  __shared__ double2 snv[kGmresMax];
-  if (st->h.done) {  // the same value in every thread: nothing below writes it before this point
-    if (threadIdx.x == 0) st->h.inv_h = 0.0;
+  if (st->done) {  // the same value in every thread: nothing below writes it before this point
+    if (threadIdx.x == 0) st->inv_h = 0.0;
     return;
   }
   const int m = j + 1;  // vectors the two passes ran over
+  double2* col = st->Hc + (long long)j * (kGmresMax + 1);
   for (int i = threadIdx.x; i < m; i += kGsThreads) {
     double re = 0.0, im = 0.0;
     for (int q = 0; q < S; ++q) {
@@ -314,91 +341,19 @@ k_gmres_step(int j, const double* __restrict__ part1, const double* __restrict__
       im += part1[((long long)q * m + i) * 2 + 1] + part2[((long long)q * m + i) * 2 + 1];
     }
     col[i] = make_double2(re, im);
-    if (i < j) {
-      csv[i] = st->cs[i];
-      snv[i] = st->sn[i];
-    }
   }
-  const double h = sqrt(fmax(gs_sum_partials(nrm_part, nb, red), 0.0));  // synchronises: col, csv, snv complete
+  const double h = sqrt(fmax(gs_sum_partials(nrm_part, nb, red), 0.0));
   if (threadIdx.x == 0) {
-    // the earlier rotations [[c, s], [-conj(s), c]] on the new column, carried
-    // down the column in registers
-    double2 x = col[0];
-    for (int i = 0; i < j; ++i) {
-      const double2 y = col[i + 1];
-      const double c = csv[i];
-      const double2 sn = snv[i];
-      col[i] = cadd(cscale(x, c), cmul(sn, y));
-      x = csub(cscale(y, c), cmulc(sn, x));
-    }
-    // the rotation that zeroes h_{j+1,j}
-    const double2 a = x, b = make_double2(h, 0.0);
-    const double na = sqrt(cabs2(a)), nbv = h;
-    double c;
-    double2 sn;
-    if (nbv == 0.0) {
-      c = 1.0;
-      sn = make_double2(0.0, 0.0);
-    } else if (na == 0.0) {
-      c = 0.0;
-      sn = make_double2(1.0, 0.0);  // conj(b) / |b| with b = h > 0
-    } else {
-      const double r = hypot(na, nbv);
-      c = na / r;
-      sn = cscale(make_double2(a.x / na, a.y / na), nbv / r);  // (a / |a|) conj(b) / r, b = h real
-    }
-    st->cs[j] = c;
-    st->sn[j] = sn;
-    col[j] = cadd(cscale(a, c), cmul(sn, b));
-    col[j + 1] = make_double2(0.0, 0.0);
-    const double2 gj = st->g[j];
-    st->g[j] = cscale(gj, c);
-    const double2 g1 = cneg(cmulc(sn, gj));
-    st->g[j + 1] = g1;
-    const double res = sqrt(cabs2(g1));
-    st->h.k = j + 1;
-    st->h.resid = res;
-    const bool done = res <= tolb || h == 0.0;
-    st->h.done = done ? 1 : 0;
-    st->h.inv_h = done ? 0.0 : 1.0 / h;
+    col[j + 1] = make_double2(h, 0.0);
+    st->done = h == 0.0 ? 1 : 0;
+    st->inv_h = h > 0.0 ? 1.0 / h : 0.0;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= j + 1; i += kGsThreads) st->H[i * kGmresMax + j] = col[i];
 }
 
 __global__ void k_gmres_store(const double2* __restrict__ w, double2* __restrict__ dst, const GmresDev* st, long long N) {
-  const double sc = st->h.inv_h;
+  const double sc = st->inv_h;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     dst[i] = cscale(w[i], sc);
-}
-
-// one warp: back substitution over the k columns, lanes split each row's sum
-__global__ void k_gmres_solve(GmresDev* st) {
-  __shared__ double2 ys[kGmresMax];
-  const int k = st->h.k, lane = threadIdx.x;
-  const double2* H = st->H;
-  for (int i = k - 1; i >= 0; --i) {
-    double re = 0.0, im = 0.0;
-    for (int q = i + 1 + lane; q < k; q += 32) {
-      const double2 t = cmul(H[i * kGmresMax + q], ys[q]);
-      re += t.x;
-      im += t.y;
-    }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) {
-      const double2 acc = csub(st->g[i], make_double2(re, im));
-      const double2 d = H[i * kGmresMax + i];
-      if (cabs2(d) == 0.0) {
-        st->h.status = -7;
-        ys[i] = make_double2(0.0, 0.0);
-      } else {
-        ys[i] = cdiv(acc, d);
-      }
-    }
-    __syncwarp();
-  }
-  for (int q = lane; q < k; q += 32) st->y[q] = ys[q];
 }
 
 int blocks_for(long long work) { return (int)std::max<long long>(1, std::min<long long>((work + 255) / 256, 152LL * 16)); }
@@ -506,6 +461,13 @@ int gs_chunks(long long N) {
 
 int gs_norm_blocks(long long N) { return blocks_for(N); }
 
+// vectors shorter than this split the basis sum of gs_axpy across blocks
+constexpr long long kGsSplitN = 152LL * 2 * kGsThreads;
+
+long long gs_axpy_tmp_len(long long N) {
+  return N < kGsSplitN ? (long long)((kGmresMax + kGsAxpyChunk - 1) / kGsAxpyChunk) * N : 0;
+}
+
 cudaError_t gs_dots(const double2* V, int m, const double2* w, long long N, double* part, cudaStream_t s) {
   if (m <= 0 || m > kGmresMax) return cudaErrorInvalidValue;
   const int S = gs_chunks(N);
@@ -516,36 +478,36 @@ cudaError_t gs_dots(const double2* V, int m, const double2* w, long long N, doub
 }
 
 cudaError_t gs_axpy(double2* w, const double2* V, long long N, int m, const double* part, double* nrm_part,
-                    cudaStream_t s) {
+                    double2* tmp, cudaStream_t s) {
   if (m <= 0 || m > kGmresMax) return cudaErrorInvalidValue;
-  k_gs_axpy<<<gs_norm_blocks(N), kGsThreads, 0, s>>>(w, V, N, m, part, gs_chunks(N), nrm_part);
+  if (N < kGsSplitN) {
+    if (tmp == nullptr) return cudaErrorInvalidValue;
+    const int JC = (m + kGsAxpyChunk - 1) / kGsAxpyChunk;
+    k_gs_axpy_part<<<dim3((unsigned)((N + kGsThreads - 1) / kGsThreads), JC), kGsThreads, 0, s>>>(V, N, m, part,
+                                                                                                gs_chunks(N), tmp);
+    k_gs_axpy_sum<<<gs_norm_blocks(N), kGsThreads, 0, s>>>(w, N, tmp, JC, nrm_part);
+  } else {
+    k_gs_axpy<<<gs_norm_blocks(N), kGsThreads, 0, s>>>(w, V, N, m, part, gs_chunks(N), nrm_part);
+  }
   return cudaGetLastError();
 }
+
+int gs_axpy_kernels(long long N) { return N < kGsSplitN ? 2 : 1; }
 
 cudaError_t gmres_residual(const double2* b, double2* w, long long N, double* nrm_part, cudaStream_t s) {
   k_gmres_residual<<<gs_norm_blocks(N), kGsThreads, 0, s>>>(b, w, N, nrm_part);
   return cudaGetLastError();
 }
 
-cudaError_t gmres_start(const double* nrm_part, int nb, GmresDev* st, double tolb, cudaStream_t s) {
-  k_gmres_start<<<1, kGsThreads, 0, s>>>(nrm_part, nb, st, tolb);
-  return cudaGetLastError();
-}
-
-cudaError_t gmres_step(int j, const double* part1, const double* part2, int S, const double* nrm_part, int nb,
-                       GmresDev* st, double tolb, cudaStream_t s) {
+cudaError_t gmres_column(int j, const double* part1, const double* part2, int S, const double* nrm_part, int nb,
+                         GmresDev* st, cudaStream_t s) {
   if (j < 0 || j >= kGmresMax) return cudaErrorInvalidValue;
-  k_gmres_step<<<1, kGsThreads, 0, s>>>(j, part1, part2, S, nrm_part, nb, st, tolb);
+  k_gmres_column<<<1, kGsThreads, 0, s>>>(j, part1, part2, S, nrm_part, nb, st);
   return cudaGetLastError();
 }
 
 cudaError_t gmres_store(const double2* w, double2* dst, const GmresDev* st, long long N, cudaStream_t s) {
   k_gmres_store<<<blocks_for(N), 256, 0, s>>>(w, dst, st, N);
-  return cudaGetLastError();
-}
-
-cudaError_t gmres_solve(GmresDev* st, cudaStream_t s) {
-  k_gmres_solve<<<1, 32, 0, s>>>(st);
   return cudaGetLastError();
 }
 

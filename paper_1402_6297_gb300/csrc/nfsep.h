@@ -40,31 +40,20 @@ cudaError_t zscale_copy(const double2* src, double2* dst, double scale, long lon
 // V_i <- sum_{r<m} V_r Y[r k + i], i < k, in place (Y device interleaved complex)
 cudaError_t zrotate(double2* V, int m, const double* Y, int k, long long N, cudaStream_t s);
 
-// Restarted GMRES with the projected problem on the device (the library's
-// inner solver for (M - sigma I) z = b): the Gram-Schmidt coefficients, the
-// Hessenberg matrix, its Givens rotations and the back substitution stay in
-// device memory, so a GMRES cycle is enqueued without a host round trip per
-// step.  The iteration is that of nfs::host::gmres (krylov.h): two classical
-// Gram-Schmidt passes per step, stop at |g_{j+1}| <= tol ||b|| (the residual
-// norm of the small least-squares problem) or h_{j+1,j} = 0.
+// Restarted GMRES for the shifted systems (M - sigma I) z = b with the long-
+// vector work on the device and no host round trip per step: the two
+// classical Gram-Schmidt passes write their coefficients to device memory
+// and the updates read them there, and a one-block kernel per step forms
+// the Hessenberg column and the scale of the next basis vector.  The host
+// reads a batch of columns at once and keeps the small least-squares problem
+// (nfs::host::GivensLS, krylov.h).
 constexpr int kGmresMax = 128;  // largest restart length
-struct GmresHeader {  // what the host reads between batches of steps
-  int done;       // 1 once converged or h_{j+1,j} = 0; the cycle's later steps are no-ops
-  int k;          // columns of the current cycle
-  int status;     // 0, or -7 if the back substitution met a zero pivot
-  int pad;
-  double inv_h;   // scale of the vector stored next: 1 / h_{j+1,j}, 1 / beta, 0 once done
-  double beta;    // ||b - Op x|| at the start of the cycle
-  double resid;   // |g_k|: the cycle's estimate of ||b - Op x||
-  double pad2;
-};
 struct GmresDev {
-  GmresHeader h;
-  double cs[kGmresMax];
-  double2 sn[kGmresMax];
-  double2 g[kGmresMax + 1];
-  double2 y[kGmresMax];
-  double2 H[(kGmresMax + 1) * kGmresMax];  // H(i, j) at H[i * kGmresMax + j]
+  int done;       // 1 once h_{j+1,j} = 0 (an invariant Krylov space): later steps of the cycle store zeros
+  int pad[3];
+  double inv_h;   // 1 / h_{j+1,j} of the last step, 0 once done
+  double pad2;
+  double2 Hc[kGmresMax * (kGmresMax + 1)];  // column j of H at Hc[j (kGmresMax + 1) + i], i <= j + 1
 };
 
 // Chunks (S) of the Gram-Schmidt dot products for vectors of length N, and
@@ -73,23 +62,24 @@ int gs_chunks(long long N);
 int gs_norm_blocks(long long N);
 // part[(s m + j) 2 + {0, 1}] = chunk s's share of V_j^* w, j < m (m <= kGmresMax)
 cudaError_t gs_dots(const double2* V, int m, const double2* w, long long N, double* part, cudaStream_t s);
+// complex128 elements of the scratch gs_axpy needs for vectors of length N
+// and m <= kGmresMax basis vectors (0: none)
+long long gs_axpy_tmp_len(long long N);
 // w -= sum_{j<m} c_j V_j with c_j = sum_s part[(s m + j)]; with nrm_part,
-// nrm_part[b] = block b's share of ||w||^2 after the update
+// nrm_part[b] = block b's share of ||w||^2 after the update.  Short vectors
+// split the sum over the basis across blocks (partial sums in tmp) so that
+// enough of the GPU works on it.
 cudaError_t gs_axpy(double2* w, const double2* V, long long N, int m, const double* part, double* nrm_part,
-                    cudaStream_t s);
+                    double2* tmp, cudaStream_t s);
+int gs_axpy_kernels(long long N);  // kernel launches one gs_axpy makes
 // w = b - w and the partials of ||w||^2
 cudaError_t gmres_residual(const double2* b, double2* w, long long N, double* nrm_part, cudaStream_t s);
-// Start of a cycle: beta = ||w|| from nb partials, g = beta e_0, done if
-// beta <= tolb, inv_h = 1 / beta
-cudaError_t gmres_start(const double* nrm_part, int nb, GmresDev* st, double tolb, cudaStream_t s);
 // Step j: column j of H from the two passes' partials (S chunks each, over
-// j + 1 vectors) and h_{j+1,j} from nb norm partials; the earlier rotations,
-// a new one, g, k = j + 1, done and inv_h.  No-op once done.
-cudaError_t gmres_step(int j, const double* part1, const double* part2, int S, const double* nrm_part, int nb,
-                       GmresDev* st, double tolb, cudaStream_t s);
+// j + 1 vectors) and h_{j+1,j} from nb norm partials; inv_h and done.  A
+// no-op once done.
+cudaError_t gmres_column(int j, const double* part1, const double* part2, int S, const double* nrm_part, int nb,
+                         GmresDev* st, cudaStream_t s);
 // dst = inv_h * w
 cudaError_t gmres_store(const double2* w, double2* dst, const GmresDev* st, long long N, cudaStream_t s);
-// y = R^{-1} g over the k columns of the cycle
-cudaError_t gmres_solve(GmresDev* st, cudaStream_t s);
 
 }  // namespace nfs
