@@ -88,6 +88,9 @@ def parse():
     p.add_argument("--skip-sphere64", action="store_true", help="skip the 64^3 FP64 sphere leg (config 2)")
     p.add_argument("--matvec-only", action="store_true",
                    help="time only the A_r products (profiling aid; prints a reduced line)")
+    p.add_argument("--profile-grid", type=int, default=0,
+                   help="profiling aid: only mixed eigensolves (nev 10) of the headline medium on an "
+                        "N^3 grid, a few GB on the device; prints a reduced line")
     return p.parse_args()
 
 
@@ -379,6 +382,12 @@ def batch_leg(nfs, wl, torch):
         ctx.close()
         diffs[str(size)] = float((abs(om1 - omega[i]) / om1).max())  # per eigenvalue
     seq_total = 16 * sum(seq.values())
+    # the oracle's stored eigenvalues of one problem per grid size, where written
+    vs_oracle = {}
+    for i in (5, 21, 37):
+        ref = golden_values(f"bz48_{i}")
+        if ref is not None:
+            vs_oracle[str(i)] = float(max(abs(a - b) / b for a, b in zip(omega[i], ref["omega"])))
     return {"workload": "bz48: 48 k-points on G-X-M-R-G, 16 each at 32^3/48^3/64^3, chiral spheres r 0.25, "
                         "gamma U[0.2,0.8], nev 10, mixed", "classes": classes, "seconds": dt,
             "eigenpairs_per_s": len(probs) * nev / dt,
@@ -387,7 +396,8 @@ def batch_leg(nfs, wl, torch):
             "lanczos_steps_max": int(max(i.lanczos_steps for i in infos)),
             "max_rel_diff_vs_single": diffs,  # max_i |omega_i(batch) - omega_i(alone)| / omega_i
             "sequential_estimate_s": seq_total, "speedup_vs_sequential": seq_total / dt,
-            "sequential_sample_s": {str(k): v for k, v in seq.items()}}
+            "sequential_sample_s": {str(k): v for k, v in seq.items()},
+            "max_rel_err_vs_oracle": vs_oracle or None}  # problem index -> max_i |omega_i - oracle_i| / oracle_i
 
 
 def grad_leg(nfs, wl, torch, np):
@@ -605,6 +615,24 @@ def run_ours(args):
     n = n1 * n2 * n3
     hbm, peak_kind = peaks()
     stream = torch.cuda.current_stream()
+
+    if args.profile_grid:
+        g = (args.profile_grid,) * 3
+        pc = nfs.Context(g, kd, wl.pseudochiral_cylinders(g, 4, 0.1, 13.0, 1.0, 0.4, (0, 1), 0), precision="mixed",
+                         cg_tol=1e-10, eig_tol=1e-10)
+        for _ in range(args.warmup):
+            pc.eigs(10, vectors=False, allow_noconv=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, _, pinfo = pc.eigs(10, vectors=False, allow_noconv=True)
+        torch.cuda.synchronize()
+        pc.close()
+        if rank == 0:
+            print(json.dumps({"mode": "profile-grid", "grid": list(g), "nev": 10,
+                              "s_per_eigensolve": (time.perf_counter() - t0) / max(1, args.steps),
+                              "lanczos_steps": pinfo.lanczos_steps, "seconds_orth": pinfo.seconds_orth}), flush=True)
+        return 0
 
     ctx = nfs.Context(grid, kd, med, precision="mixed", cg_tol=1e-10, eig_tol=1e-10)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)

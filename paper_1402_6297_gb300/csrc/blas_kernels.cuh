@@ -590,6 +590,10 @@ k_exact_dots(const float2* __restrict__ Shi, const float2* __restrict__ Slo, lon
       }
     }
   }
+  // block sums in FP64.  (Double-single sums on the FP32 units would free
+  // the FP64 pipe, which these sums keep ~70% busy at small sizes, but they
+  // lost the accuracy the monitor needs on homogeneous media at symmetric
+  // k-points: spurious losses of 1e-6 and wrong degenerate eigenvalues.)
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const double sr = block_sum<kRedThreads>((double)acc[g].hi.x + (double)acc[g].lo.x + (double)small[g].x);

@@ -2,6 +2,8 @@
 // shared by the vector kernels (blas_kernels.cuh) and the product pass that
 // can take the CG step itself (matvec_kernels.cuh).  Declarations only.
 #pragma once
+#include <type_traits>
+
 #include "nfs_complex.cuh"
 
 namespace nfs {
@@ -54,5 +56,89 @@ struct Acc<float2> {
   }
   __device__ __forceinline__ double total() const { return d + (double)f; }
 };
+
+// Per-thread accumulator and block sum of the CG reductions (the partials
+// of p^* A p and r^* r).  Complex64 runs accumulate in double-single
+// arithmetic on the FP32 units (hi + lo floats, TwoSum: ~1e-14 of the sum of
+// the terms' magnitudes) and complex128 runs in FP64.  FP64 arithmetic is
+// scarce on this GPU: a block sum of doubles in every CTA of a pass keeps
+// the SM's FP64 pipe busy for microseconds.
+template <typename T>
+struct RedAcc;
+template <>
+struct RedAcc<double> {
+  using value_type = double;
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_double(double x) { v += x; }
+  // the block's total, valid in thread 0; all threads must call it
+  template <int NT>
+  __device__ __forceinline__ double block_total() {
+    __shared__ double sh[NT / 32];
+    double t = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = t;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+      r = lane < NT / 32 ? sh[lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+  }
+};
+template <>
+struct RedAcc<float> {
+  using value_type = float;
+  float hi = 0.f, lo = 0.f;
+  // (hi, lo) += (bh, bl): TwoSum of the high parts, the rest to the error, renormalised
+  __device__ __forceinline__ static void ds_add(float& hi, float& lo, float bh, float bl) {
+    const float s = hi + bh;
+    const float bb = s - hi;
+    const float e = ((hi - (s - bb)) + (bh - bb)) + (lo + bl);
+    hi = s + e;
+    lo = e - (hi - s);
+  }
+  __device__ __forceinline__ void add(float x) {
+    const float s = hi + x;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+  }
+  // a partial stored as a double, split into two floats
+  __device__ __forceinline__ void add_double(double x) {
+    const float h = (float)x;
+    ds_add(hi, lo, h, (float)(x - (double)h));
+  }
+  template <int NT>
+  __device__ __forceinline__ double block_total() {
+    __shared__ float2 sh[NT / 32];
+    float th = hi, tl = lo;
+    ds_add(th, tl, 0.f, 0.f);  // renormalise
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      ds_add(th, tl, __shfl_xor_sync(0xffffffffu, th, o), __shfl_xor_sync(0xffffffffu, tl, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = make_float2(th, tl);
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+      float rh = lane < NT / 32 ? sh[lane].x : 0.f, rl = lane < NT / 32 ? sh[lane].y : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        ds_add(rh, rl, __shfl_xor_sync(0xffffffffu, rh, o), __shfl_xor_sync(0xffffffffu, rl, o));
+      if (lane == 0) r = (double)rh + (double)rl;
+    }
+    __syncthreads();
+    return r;
+  }
+};
+// the accumulator for data of real type R (complex64 or complex128 runs)
+template <typename R>
+using RedAccFor = RedAcc<typename std::conditional<std::is_same<R, float>::value, float, double>::type>;
 
 }  // namespace nfs

@@ -522,7 +522,7 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
                                                          NoPut{});
   // CG curvature from the real-space fields (Parseval; the DFTs carry the
   // factor n that inv_n removes): u^* A_r u = sum Re(conj(P) f + conj(Q) w)
-  double dot_acc = 0.0;
+  RedAccFor<R> dot_acc;
   for (int idx = threadIdx.x; idx < N3 * TX; idx += NT) {
     const int c = idx % TX, z = idx / TX;
     C* row = buf + z * PITCH + c;
@@ -535,7 +535,7 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         sacc += p[k].x * fo[k].x + p[k].y * fo[k].y + q[k].x * wo[k].x + q[k].y * wo[k].y;
-      dot_acc += (double)sacc;
+      dot_acc.add(static_cast<typename RedAccFor<R>::value_type>(sacc));
     }
     row[0] = fo[0];
     row[TX] = fo[1];
@@ -545,7 +545,7 @@ k_pass2_z_material(cplx<R>* __restrict__ fld, MatView<R> mat, const cplx<R>* __r
     row[5 * TX] = wo[2];
   }
   if (dot_part != nullptr) {
-    const double tot = block_sum_dbl<NT>(dot_acc);  // (its barriers also order the material writes)
+    const double tot = dot_acc.template block_total<NT>();  // (its barriers also order the material writes)
     if (threadIdx.x == 0) dot_part[(long long)prob * bs.sstate + blockIdx.x % tiles] = tot;
   } else {
     __syncthreads();
@@ -595,9 +595,9 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   constexpr bool CGT = std::is_same<R, float>::value || std::is_same<R, double>::value;
   CGState* cst = (CGT && cg.st != nullptr) ? cg.st + prob : nullptr;
   if (cst != nullptr) {
-    double v = 0.0;
-    for (int i = threadIdx.x; i < cst->npart_a; i += NT) v += cst->part_a[i];
-    const double pAp = block_sum_dbl<NT>(v);
+    RedAccFor<R> pa;
+    for (int i = threadIdx.x; i < cst->npart_a; i += NT) pa.add_double(cst->part_a[i]);
+    const double pAp = pa.template block_total<NT>();
     if (threadIdx.x == 0) {
       s_cg_alpha = cst->rr / pAp;
       s_cg_ok = (pAp > 0.0) && (s_cg_alpha == s_cg_alpha);  // also catches NaN
@@ -629,8 +629,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
   const bool cg_upd = cg_on && s_cg_ok;
   const R cg_al = cg_on ? (R)s_cg_alpha : (R)0;
   const long long cg_off = prob * bs.su + (2 * grp) * n + (long long)i3 * NE;
-  using AccT = typename std::conditional<CGT, C, double2>::type;
-  Acc<AccT> cg_acc;
+  RedAccFor<R> cg_acc;
   // EPV consecutive elements per lane (e0, e1 even)
   for (int ev = e0 / EPV + (int)threadIdx.x; ev < e1 / EPV; ev += NT) {
     C r0[EPV], r1[EPV];
@@ -668,7 +667,8 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
           cg.x[i1] = xb;
           cg.r[i0] = ra;
           cg.r[i1] = rb;
-          cg_acc.add(ra.x * ra.x + ra.y * ra.y + rb.x * rb.x + rb.y * rb.y);
+          cg_acc.add(static_cast<typename RedAccFor<R>::value_type>(ra.x * ra.x + ra.y * ra.y + rb.x * rb.x +
+                                                                   rb.y * rb.y));
         }
       }
     } else if constexpr (EPV == 2) {
@@ -685,7 +685,7 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
     // iteration count and the convergence state for the next launch
     const int ncta = 6 * n3;
     const int cta = rank + 3 * (grp + 2 * i3);
-    const double part = block_sum_dbl<NT>(cg_acc.total());
+    const double part = cg_acc.template block_total<NT>();
     if (threadIdx.x == 0) {
       cst->part_b[cta] = part;
       __threadfence();
@@ -694,9 +694,9 @@ k_pass3_fft_xy_project(const cplx<R>* __restrict__ fld, cplx<R>* __restrict__ Au
     __syncthreads();
     if (s_cg_last) {
       __threadfence();
-      double v = 0.0;
-      for (int i = threadIdx.x; i < ncta; i += NT) v += ((volatile double*)cst->part_b)[i];
-      const double rr = block_sum_dbl<NT>(v);
+      RedAccFor<R> rb_acc;
+      for (int i = threadIdx.x; i < ncta; i += NT) rb_acc.add_double(((volatile double*)cst->part_b)[i]);
+      const double rr = rb_acc.template block_total<NT>();
       if (threadIdx.x == 0) {
         cst->arrived = 0;
         if (!s_cg_ok) {

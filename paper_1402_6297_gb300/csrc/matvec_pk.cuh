@@ -429,7 +429,7 @@ k_pk_pass2(float2* __restrict__ fld, MatView<float> mat, const float2* __restric
     const int idx = threadIdx.x + b * NT;
     if ((N3 * TX) % NT == 0 || idx < N3 * TX) mv[b].load(mat, (long long)(idx / TX) * ncols + col0 + idx % TX);
   }
-  double dot_acc = 0.0;
+  RedAcc<float> dot_acc;
 #pragma unroll
   for (int b = 0; b < MV; ++b) {
     const int idx = threadIdx.x + b * NT;
@@ -449,13 +449,13 @@ k_pk_pass2(float2* __restrict__ fld, MatView<float> mat, const float2* __restric
       float sacc = 0.f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) sacc += p[k].x * f[k].x + p[k].y * f[k].y + q[k].x * w[k].x + q[k].y * w[k].y;
-      dot_acc += (double)sacc;
+      dot_acc.add(sacc);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) cell[k * TX] = {f2pk(f[k].x, w[k].x), f2pk(f[k].y, w[k].y)};
   }
   if (dot_part != nullptr) {
-    const double tot = block_sum_dbl<NT>(dot_acc);  // its barriers also order the material writes
+    const double tot = dot_acc.block_total<NT>();  // its barriers also order the material writes
     if (threadIdx.x == 0) dot_part[(long long)prob * bs.sstate + blockIdx.x % tiles] = tot;
   } else {
     __syncthreads();

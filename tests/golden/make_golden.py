@@ -143,11 +143,33 @@ def nfsep_grid(n):
             f.write(f"{w.real:.17e} {w.imag:.17e}\n")
 
 
+def bz48_problem(i):
+    """The 10 smallest positive eigenvalues of problem i of the bz48 batch
+    (48 k-points on G-X-M-R-G over 32^3, 48^3 and 64^3 chiral spheres) by
+    the FFT NFGEP (tier O3), with the wall time and A_r products recorded."""
+    w = wl.workload("bz48")
+    g, k, med, nev = w["grid"][i], tuple(float(x) for x in w["kdota"][i]), w["medium"][i], w["nev"]
+    O = nfgep.NFGEP(g, k, med)
+    t0 = time.time()
+    om, _ = O.eigs(nev, tol=1e-12, cg_tol=1e-13)
+    dt = time.time() - t0
+    write(f"bz48_{i}_omega.txt", f"""
+{nev} smallest positive eigenvalues omega of the discrete GEP (Sec. 3, eq. (discrete_GEP_EH)),
+ascending; problem {i} of workload bz48: grid {g[0]}x{g[1]}x{g[2]}, a = 1, k.a = {k},
+chiral sphere of radius 0.25 centred in the cell, eps 13 inside, 1 outside, mu = 1,
+gamma drawn per k-point (workloads.bz48)
+oracle tier O3: FFT NFGEP (oracle.nfgep.NFGEP.eigs: ARPACK invert Lanczos, ncv {max(3 * nev, 2 * nev + 1)},
+tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s on one host core
+""", om)
+
+
 if __name__ == "__main__":
     if len(sys.argv) > 1:
         for name in sys.argv[1:]:
             if name.startswith("nfsep"):
                 nfsep_grid(int(name[5:]))
+            elif name.startswith("bz48_"):
+                bz48_problem(int(name[5:]))
             else:
                 large(name)
     else:
