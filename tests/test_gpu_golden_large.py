@@ -2,7 +2,9 @@
 
 tests/golden/sphere64_omega.txt and pseudo96_omega.txt hold the 20 smallest
 positive eigenvalues of the 64^3 chiral sphere (sphere64) and of the 96^3
-pseudochiral cylinders (pseudo96, the headline workload), written by
+pseudochiral cylinders (pseudo96, the headline workload), and
+bz48_<i>_omega.txt the 10 smallest of problem i of the 48-k-point batch
+(bz48: one problem per grid size 32^3, 48^3, 64^3), written by
 tests/golden/make_golden.py with the oracle's FFT NFGEP (tier O3: ARPACK invert
 Lanczos with CG at 1e-13, tolerance 1e-12).  The FP64 GPU path must match them
 to 1e-10 relative and the mixed-precision path to 1e-8 (with residual
@@ -10,7 +12,9 @@ to 1e-10 relative and the mixed-precision path to 1e-8 (with residual
 configuration the benchmark times (default options, nev 20).  A residual alone
 cannot show that these are the 20 smallest eigenvalues; the oracle list can."""
 
+import glob
 import os
+import re
 
 import numpy as np
 import pytest
@@ -43,3 +47,22 @@ def _check(lib, name, precision, tol):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_sphere64_vs_oracle(lib, precision, tol):
     _check(lib, "sphere64", precision, tol)
+
+
+def test_bz48_batch_vs_oracle(lib):
+    """The whole 48-problem batch as the benchmark runs it (three grid classes
+    solved concurrently, mixed precision), against the oracle's eigenvalues of
+    the problems it has stored."""
+    w = wl.workload("bz48")
+    refs = {}
+    for path in glob.glob(os.path.join(HERE, "golden", "bz48_*_omega.txt")):
+        refs[int(re.search(r"bz48_(\d+)_omega", path).group(1))] = np.loadtxt(path)
+    assert refs, "no stored bz48 eigenvalues"
+    probs = [(g, tuple(float(x) for x in k), m) for g, k, m in zip(w["grid"], w["kdota"], w["medium"])]
+    b = lib.Batch(probs, precision="mixed", cg_tol=1e-10, eig_tol=1e-10)
+    omega, infos = b.eigs(w["nev"])
+    b.close()
+    assert all(i.nconv >= w["nev"] for i in infos)
+    for i, ref in refs.items():
+        rel = np.abs(omega[i] - ref) / ref
+        assert rel.max() < 1e-8, (i, rel.max(), list(omega[i]))
