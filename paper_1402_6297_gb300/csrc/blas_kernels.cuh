@@ -3,11 +3,12 @@
 // problem p's vectors sit at base + p * N (N = 4n), and the problem index comes
 // from a grid dimension, so a launch serves every problem at once.
 //
-// Reductions are deterministic: a fixed grid of kRedBlocks blocks per problem
-// writes one partial per block, and a one-block kernel sums the partials in a
-// fixed order.  Every CG kernel reads its problem's device `done` flag first
-// and returns at once when it is set, so launched iterations past convergence
-// (or for problems already converged) cost only empty launches.
+// Reductions are deterministic: a grid of blocks per problem fixed by the
+// vector length and the problem count (at most kRedBlocks) writes one
+// partial per block, and a one-block kernel sums the partials in a fixed
+// order.  Every CG kernel reads its problem's device `done` flag first and
+// returns at once when it is set, so launched iterations past convergence (or
+// for problems already converged) cost only empty launches.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -47,7 +48,7 @@ __device__ __forceinline__ double sum_partials(const double* part, int count = k
   return block_sum<kRedThreads>(v);
 }
 
-// part[p * pstride + b] = block b's share of Re(conj(x_p) y_p); grid (kRedBlocks, P).
+// part[p * pstride + b] = block b's share of Re(conj(x_p) y_p); grid (blocks, P).
 // skip (optional): problem p is skipped when skip[p * sstride] is nonzero.
 template <typename C>
 __global__ void __launch_bounds__(kRedThreads)
@@ -87,11 +88,12 @@ k_residual_parts(const double2* __restrict__ Ay, const double2* __restrict__ By,
   }
 }
 
-// CG start, one block per problem: rr = sum part_a; stop once r^* r <= tol2[p].
+// CG start, one block per problem: rr = the sum of the nred partials in
+// part_a; stop once r^* r <= tol2[p].
 __global__ void __launch_bounds__(kRedThreads)
-k_cg_init(CGState* st, const double* __restrict__ tol2, int maxit, int npart_a) {
+k_cg_init(CGState* st, const double* __restrict__ tol2, int maxit, int npart_a, int nred) {
   st += blockIdx.x;
-  const double rr = sum_partials(st->part_a);
+  const double rr = sum_partials(st->part_a, nred);
   if (threadIdx.x == 0) {
     const double t2 = tol2[blockIdx.x];
     st->npart_a = npart_a;
@@ -305,7 +307,7 @@ __global__ void k_random_fill(double2* __restrict__ v, long long N, long long vs
 // ---------------------------------------------------------------------------
 
 // part[((p * gridDim.x + b) * m + j) * 2 + {0,1}] = block b's share of
-// conj(V_pj)^T w_p, j < m; grid (kRedBlocks, P).
+// conj(V_pj)^T w_p, j < m; grid (blocks, P).
 template <int NT>
 __global__ void __launch_bounds__(NT)
 k_multi_dot(const double2* __restrict__ V, long long vstride, int m, const double2* __restrict__ w, long long N,
@@ -548,7 +550,7 @@ k_dots_finish(const double* __restrict__ part, int m, int nb, double* __restrict
 
 // part[(((p * m + j) * gridDim.x) + b) * 2 + {0, 1}] = block b's share of
 // conj(S_pj)^T w_p (S = Shi + Slo, w = whi + wlo) for the G vectors
-// j = blockIdx.y * G + g < m; grid (kRedBlocks, ceil(m / G), P).
+// j = blockIdx.y * G + g < m; grid (blocks, ceil(m / G), P).
 template <int G>
 __global__ void __launch_bounds__(kRedThreads)
 k_exact_dots(const float2* __restrict__ Shi, const float2* __restrict__ Slo, long long sstride, int m,

@@ -308,18 +308,36 @@ int ensure_scratch(nfs_ctx* c, size_t dlen) {
   return NFS_OK;
 }
 
+// Blocks per problem of the reductions over P problems' vectors of length N.
+// Never more blocks than the vector has threads' worth of elements (empty
+// blocks add exact zeros: a single problem's sums are the same at any larger
+// count); for batches, fewer, with at least 32 elements per thread, as long
+// as all problems together still have kRedBlocks blocks.  Each block ends in
+// FP64 block sums, which GB300 retires at about one warp instruction per 17
+// SM cycles: a full grid per problem over the short vectors of a batch of
+// small grids made those epilogues, not the data, the cost of a reduction.
+int red_blocks(long long N, int P) {
+  long long nb = std::min<long long>(kRedBlocks, (N + kRedThreads - 1) / kRedThreads);
+  if (P > 1) {
+    const long long per32 = (N + (long long)kRedThreads * 32 - 1) / ((long long)kRedThreads * 32);
+    nb = std::min(nb, std::max<long long>(per32, (kRedBlocks + P - 1) / P));
+  }
+  return (int)std::max<long long>(1, nb);
+}
+
 // Re(x_p^* y_p) for every problem, on the host
 template <typename C>
 int dots_re(nfs_ctx* c, cudaStream_t s, const C* x, const C* y, std::vector<double>& out) {
-  nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(x, y, c->N, c->dscratch, kRedBlocks, nullptr, 0);
+  const int nb = red_blocks(c->N, c->P);
+  nfs::k_dot_re<C><<<dim3(nb, c->P), kRedThreads, 0, s>>>(x, y, c->N, c->dscratch, nb, nullptr, 0);
   CK(cudaGetLastError());
   c->launches += 1;
-  CK(cudaMemcpyAsync(c->hscratch, c->dscratch, (size_t)kRedBlocks * c->P * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->hscratch, c->dscratch, (size_t)nb * c->P * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   out.assign(c->P, 0.0);
   for (int p = 0; p < c->P; ++p) {
     double t = 0.0;
-    for (int i = 0; i < kRedBlocks; ++i) t += c->hscratch[(size_t)p * kRedBlocks + i];
+    for (int i = 0; i < nb; ++i) t += c->hscratch[(size_t)p * nb + i];
     out[p] = t;
   }
   return NFS_OK;
@@ -439,11 +457,11 @@ int cg_run(nfs_ctx* c, nfs::cplx<R>* x, nfs::cplx<R>* r, nfs::cplx<R>* p, nfs::c
   CK(cudaStreamSynchronize(s));  // earlier work is not the loop's
   const double t0 = now_s();
   CK(cudaMemsetAsync(p, 0, c->P * c->N * sizeof(C), s));  // with beta = 0 the first pass 1 sets p = r
-  nfs::k_dot_re<C><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(r, r, c->N, c->st->part_a, nfs::kStateDoubles,
-                                                                   nullptr, 0);
+  const int nb = red_blocks(c->N, c->P);
+  nfs::k_dot_re<C><<<dim3(nb, c->P), kRedThreads, 0, s>>>(r, r, c->N, c->st->part_a, nfs::kStateDoubles, nullptr, 0);
   TRY(put_small(c, s, 0, tol2));
   nfs::k_cg_init<<<c->P, kRedThreads, 0, s>>>(c->st, c->d_small, maxit,
-                                               nfs::matvec_dot_partials<R>(c->n1, c->n2, c->n3));
+                                               nfs::matvec_dot_partials<R>(c->n1, c->n2, c->n3), nb);
   CK(cudaGetLastError());
   c->launches += 2;
   cudaGraphExec_t exec = nullptr;
@@ -610,9 +628,10 @@ int multi_dot(nfs_ctx* c, const double2* Vbase, int j0, int m, const double2* w,
   const long long vstride = (long long)c->vcap * c->N;
   double* part = c->dscratch;
   double* fin = c->dscratch + off_fin(c);
-  nfs::k_multi_dot<kRedThreads><<<dim3(kRedBlocks, c->P), kRedThreads, 0, s>>>(Vbase + (long long)j0 * c->N, vstride,
+  const int nb = red_blocks(c->N, c->P);
+  nfs::k_multi_dot<kRedThreads><<<dim3(nb, c->P), kRedThreads, 0, s>>>(Vbase + (long long)j0 * c->N, vstride,
                                                                               m, w, c->N, part, d_active);
-  nfs::k_multi_dot_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
+  nfs::k_multi_dot_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, nb, fin, d_active);
   CK(cudaGetLastError());
   c->launches += 2;
   CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -654,9 +673,10 @@ int exact_dots(nfs_ctx* c, int m, const double2* w, std::vector<double>& out, co
   float2* whi = c->x32 ? c->x32 : reinterpret_cast<float2*>(c->Ap64);
   float2* wlo = c->x32 ? c->r32 : reinterpret_cast<float2*>(c->Ap64) + c->P * c->N;
   nfs::k_split_hi_lo<<<grid_blocks(c->P * c->N, 256), 256, 0, s>>>(w, whi, wlo, c->P * c->N);
-  nfs::k_exact_dots<G><<<dim3(kRedBlocks, (m + G - 1) / G, c->P), kRedThreads, 0, s>>>(c->MV32, c->MV32lo, vstride, m,
+  const int nb = red_blocks(c->N, c->P);
+  nfs::k_exact_dots<G><<<dim3(nb, (m + G - 1) / G, c->P), kRedThreads, 0, s>>>(c->MV32, c->MV32lo, vstride, m,
                                                                                        whi, wlo, c->N, part, d_active);
-  nfs::k_dots_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, kRedBlocks, fin, d_active);
+  nfs::k_dots_finish<<<dim3(m, c->P), kRedThreads, 0, s>>>(part, m, nb, fin, d_active);
   CK(cudaGetLastError());
   c->launches += 3;
   CK(cudaMemcpyAsync(c->hscratch, fin, (size_t)c->P * m * 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
