@@ -72,3 +72,16 @@ def test_nfsep_eigs_nearest_shift(lib):
     for j in range(4):
         assert gep.gep_residual(g, K, med, om[j], X[j]) < 1e-8
     ctx.close()
+
+
+def test_nfsep_eigs_16_vs_oracle(lib):
+    """The same sphere on 16^3 (the bench's second NFSEP size): the four
+    eigenvalues nearest 2 + 0.1i against the oracle's stored ones."""
+    g = (16, 16, 16)
+    ref = np.loadtxt(os.path.join(os.path.dirname(GOLDEN), "nfsep16_omega.txt"))
+    ref = ref[:, 0] + 1j * ref[:, 1]
+    ctx = lib.NFSEPContext(g, K, CASES[0][2](g), eig_tol=1e-10, cg_tol=1e-12, cg_maxit=20000, max_restarts=20)
+    om, _, info = ctx.eigs(4, 2.0 + 0.1j, vectors=False)
+    ctx.close()
+    assert info.nconv == 4
+    assert rel_err(om, ref) < 1e-9, (om, ref)
