@@ -742,8 +742,12 @@ int rotate(nfs_ctx* c, double2* base, int m, const std::vector<double>& Y, int k
   }
   CK(cudaMemcpyAsync(c->dY, yhl.data(), need * sizeof(double), cudaMemcpyHostToDevice, c->work));
   // a tile of TE elements of all m vectors in shared memory: 32 while that
-  // fits in 200 KB, else narrower
-  constexpr int CPT = 4;
+  // fits in 200 KB, else narrower; CPT output columns per thread (measured at
+  // 96^3 with thick restarts, ncv 60: CPT 2 2.222 s, 4 2.241 s, 8 2.37 s)
+#ifndef NFS_ROT_CPT
+#define NFS_ROT_CPT 2
+#endif
+  constexpr int CPT = NFS_ROT_CPT;
   const float2* yhl_d = reinterpret_cast<const float2*>(c->dY);
   auto launch = [&](auto te) -> cudaError_t {
     constexpr int TE = decltype(te)::value;
