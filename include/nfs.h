@@ -221,7 +221,10 @@ int nfs_residuals(nfs_ctx* ctx, int m, const double* omega, const void* Y, doubl
  * itself allocates nothing.  Contexts set up with opt.ncv > 0 have it already.
  * The default size depends on nev only, never on the free device memory:
  * NFS_ENOMEM when it does not fit (choose a smaller opt.ncv, e.g. the paper's
- * 3 nev).  A later nfs_eigs with a larger basis reallocates. */
+ * 3 nev).  A later nfs_eigs with a larger basis reallocates.  On a context of
+ * nfs_setup_biiso it reserves what nfs_nfsep_eigs(ctx, nev, ...) uses instead:
+ * the Arnoldi basis (opt.ncv or max(2 nev + 2, 20) vectors), the GMRES basis
+ * and the reduction scratch. */
 int nfs_reserve(nfs_ctx* ctx, int nev);
 
 /* Gradient of sum_j weights[j] * omega_j with respect to every per-component
@@ -311,9 +314,9 @@ typedef struct {
  *   omega: HOST, 2 nev doubles (re, im), nearest sigma first.
  *   Y:     DEVICE complex128 [nev][4n] unit eigenvectors y of M, or NULL.
  * Synchronises opt.stream; allocates the Arnoldi and GMRES bases on first
- * use.  Returns NFS_ENOCONV with the results written if the restart cap is
- * hit, and NFS_ENOCONV with nothing written (info->status too) if an inner
- * GMRES solve reaches opt.cg_maxit products. */
+ * use unless nfs_reserve(ctx, nev) did.  Returns NFS_ENOCONV with the results
+ * written if the restart cap is hit, and NFS_ENOCONV with nothing written
+ * (info->status too) if an inner GMRES solve reaches opt.cg_maxit products. */
 int nfs_nfsep_eigs(nfs_ctx* ctx, int nev, const double sigma[2], double* omega, void* Y, nfs_nfsep_info* info);
 
 /* Fields of NFSEP eigenvectors (Algorithm 1, second branch): y <- S y, then

@@ -1852,9 +1852,17 @@ extern "C" int nfs_residuals(nfs_ctx* c, int m, const double* omega, const void*
   return NFS_OK;
 }
 
+namespace {
+int nfsep_reserve(nfs_ctx* c, int nev);
+}  // namespace
+
 extern "C" int nfs_reserve(nfs_ctx* c, int nev) {
   if (!c || nev <= 0 || nev >= c->N / 2) return NFS_EINVAL;
-  if (c->binv64) return NFS_EUNSUPPORTED;
+  if (c->binv64) {
+    TRY(nfsep_reserve(c, nev));
+    CK(cudaDeviceSynchronize());
+    return NFS_OK;
+  }
   const int m = lanczos_size(c, nev);
   if (m <= nev + 1) return NFS_EINVAL;
   TRY(reserve_lanczos(c, m));
@@ -2291,6 +2299,31 @@ int ensure_nfsep_bases(nfs_ctx* c, int m, int gm) {
                                                                4 * (size_t)(std::max(m, gm) + 2) + 64));
 }
 
+// Arnoldi basis size of an NFSEP eigensolve for nev values (opt.ncv or
+// max(2 nev + 2, 20), at most N - 1) and the GMRES restart length
+int nfsep_sizes(const nfs_ctx* c, int nev, int& m, int& gm) {
+  m = c->opt.ncv > 0 ? c->opt.ncv : std::max(2 * nev + 2, 20);
+  m = (int)std::min<long long>(m, c->N - 1);
+  if (m < nev + 2) return NFS_EINVAL;
+  gm = (int)std::min<long long>(kGmresRestart, c->N - 1);
+  return NFS_OK;
+}
+
+int nfsep_reserve(nfs_ctx* c, int nev) {
+  int m = 0, gm = 0;
+  TRY(nfsep_sizes(c, nev, m, gm));
+  TRY(ensure_nfsep_bases(c, m, gm));
+  // the Krylov-Schur restart rotation (at most m x m, interleaved complex)
+  const size_t need = (size_t)m * m * 2;
+  if (c->zY_len < need) {
+    if (c->zY) cudaFree(c->zY);
+    c->zY = nullptr;
+    TRY(dalloc(c, &c->zY, need));
+    c->zY_len = need;
+  }
+  return NFS_OK;
+}
+
 }  // namespace
 
 extern "C" int nfs_setup_biiso(nfs_ctx** out, const int grid[3], const double* lattice, const double k[3],
@@ -2355,10 +2388,8 @@ extern "C" int nfs_nfsep_eigs(nfs_ctx* c, int nev, const double sigma[2], double
   if (!c || !sigma || !omega || nev <= 0) return NFS_EINVAL;
   if (!c->binv64) return NFS_EUNSUPPORTED;
   if (!(std::isfinite(sigma[0]) && std::isfinite(sigma[1]))) return NFS_EINVAL;
-  int m = c->opt.ncv > 0 ? c->opt.ncv : std::max(2 * nev + 2, 20);
-  m = (int)std::min<long long>(m, c->N - 1);
-  if (m < nev + 2) return NFS_EINVAL;
-  const int gm = (int)std::min<long long>(kGmresRestart, c->N - 1);
+  int m = 0, gm = 0;
+  TRY(nfsep_sizes(c, nev, m, gm));
   TRY(ensure_nfsep_bases(c, m, gm));
   const double2 sg = make_double2(sigma[0], sigma[1]);
   const long long launches_0 = c->launches;

@@ -501,6 +501,14 @@ class NFSEPContext:
             raise ValueError(f"expected a contiguous CUDA complex128 tensor of {self.N} elements")
         return ctypes.c_void_p(t.data_ptr())
 
+    def reserve(self, nev):
+        """Allocate now what nfs_nfsep_eigs for nev values uses (nfs_reserve)."""
+        _check(lib().nfs_reserve(self.h, int(nev)), "nfs_reserve")
+
+    @property
+    def device_bytes(self):
+        return int(lib().nfs_device_bytes(self.h))
+
     def matvec(self, y, out=None):
         """M y (eq. NFSEP_org)."""
         if out is None:

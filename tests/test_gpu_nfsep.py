@@ -85,3 +85,16 @@ def test_nfsep_eigs_16_vs_oracle(lib):
     ctx.close()
     assert info.nconv == 4
     assert rel_err(om, ref) < 1e-9, (om, ref)
+
+
+def test_nfsep_reserve_then_eigs_allocates_nothing(lib):
+    """nfs_reserve on a bi-isotropic context takes the Arnoldi and GMRES bases
+    up front; the eigensolve then allocates no device memory."""
+    g = (8, 8, 8)
+    ctx = lib.NFSEPContext(g, K, CASES[0][2](g), eig_tol=1e-10, cg_tol=1e-12, cg_maxit=4000)
+    ctx.reserve(4)
+    before = ctx.device_bytes
+    om, _, info = ctx.eigs(4, 2.0 + 0.1j, vectors=False)
+    assert ctx.device_bytes == before
+    assert info.nconv == 4
+    ctx.close()
