@@ -112,6 +112,8 @@ def large(name):
                     "eps 13 inside, 1 outside, mu = 1",
         "pseudo96": "4 z-cylinders radius 0.1 with seeded centres (seed 0), eps 13 inside, 1 outside,\n"
                     "pseudochiral x-y coupling (eq. (pseudo_chiral_para_mtx)) gamma = 0.4 everywhere, mu = 1",
+        "pseudo48": "the pseudo96 medium on a 48^3 grid: 4 z-cylinders radius 0.1 with seeded centres (seed 0),\n"
+                    "eps 13 inside, 1 outside, pseudochiral x-y coupling gamma = 0.4 everywhere, mu = 1",
     }[name]
     write(f"{name}_omega.txt", f"""
 {w["nev"]} smallest positive eigenvalues omega of the discrete GEP (Sec. 3, eq. (discrete_GEP_EH)),
