@@ -1,8 +1,8 @@
 """The benchmark workloads against the oracle's stored eigenvalues.
 
-tests/golden/sphere64_omega.txt and pseudo96_omega.txt hold the 20 smallest
-positive eigenvalues of the 64^3 chiral sphere (sphere64) and of the 96^3
-pseudochiral cylinders (pseudo96, the headline workload), and
+tests/golden/sphere64_omega.txt and pseudo48_omega.txt hold the 20 smallest
+positive eigenvalues of the 64^3 chiral sphere (sphere64) and of the headline
+workload's pseudochiral cylinders on 48^3 (pseudo48), and
 bz48_<i>_omega.txt the 10 smallest of problem i of the 48-k-point batch
 (bz48: one problem per grid size 32^3, 48^3, 64^3), written by
 tests/golden/make_golden.py with the oracle's FFT NFGEP (tier O3: ARPACK invert
@@ -47,6 +47,12 @@ def _check(lib, name, precision, tol):
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_sphere64_vs_oracle(lib, precision, tol):
     _check(lib, "sphere64", precision, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_pseudo48_vs_oracle(lib, precision, tol):
+    """The headline medium (pseudochiral cylinders) on 48^3, nev 20."""
+    _check(lib, "pseudo48", precision, tol)
 
 
 def test_bz48_batch_vs_oracle(lib):
