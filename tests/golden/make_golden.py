@@ -120,7 +120,7 @@ def large(name):
 ascending; workload {name}: grid {g[0]}x{g[1]}x{g[2]}, a = 1, k.a = {tuple(w["kdota"])},
 {desc}
 oracle tier O3: FFT NFGEP (oracle.nfgep.NFGEP.eigs: ARPACK invert Lanczos, ncv {max(3 * w["nev"], 2 * w["nev"] + 1)},
-tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s on one host core
+tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s wall time on the build host
 """, om)
 
 
@@ -161,7 +161,7 @@ ascending; problem {i} of workload bz48: grid {g[0]}x{g[1]}x{g[2]}, a = 1, k.a =
 chiral sphere of radius 0.25 centred in the cell, eps 13 inside, 1 outside, mu = 1,
 gamma drawn per k-point (workloads.bz48)
 oracle tier O3: FFT NFGEP (oracle.nfgep.NFGEP.eigs: ARPACK invert Lanczos, ncv {max(3 * nev, 2 * nev + 1)},
-tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s on one host core
+tol 1e-12, CG tolerance 1e-13), FP64; {O.nmatvec} A_r products, {dt:.0f} s wall time on the build host
 """, om)
 
 
