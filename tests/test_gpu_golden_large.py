@@ -50,6 +50,15 @@ def test_sphere64_vs_oracle(lib, precision, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+def test_pseudo96_vs_oracle(lib, precision, tol):
+    """The headline workload itself, once the oracle's 96^3 solve (many hours
+    on the host) has written its eigenvalues."""
+    if not os.path.exists(os.path.join(HERE, "golden", "pseudo96_omega.txt")):
+        pytest.skip("the oracle's pseudo96 eigenvalues are not stored")
+    _check(lib, "pseudo96", precision, tol)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_pseudo48_vs_oracle(lib, precision, tol):
     """The headline medium (pseudochiral cylinders) on 48^3, nev 20."""
     _check(lib, "pseudo48", precision, tol)
